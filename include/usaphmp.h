@@ -1,0 +1,160 @@
+/*
+ * usaphmp.h -- C ABI of the GB300 library for the Uncapacitated Single
+ * Allocation p-Hub Median Problem (USApHMP): batched fitness evaluation of a
+ * population of chromosomes and the device-side step of the island GA of
+ * Benaini, Berrajaa, Boukachour and Oudani, "Solving the Uncapacitated Single
+ * Allocation p-Hub Median Problem on GPU" (arXiv 1704.06258).
+ *
+ * Problem (§3, eq. 1-5): n nodes, flows W[i][j] >= 0, unit costs
+ * C[i][k] >= 0; open exactly p hubs and allocate every node to one open hub
+ * (each hub to itself) to minimise
+ *     sum_i sum_j W[i][j] * (chi*C[i][h(i)] + alpha*C[h(i)][h(j)] + delta*C[h(j)][j]),
+ * the hub-to-hub leg taken on the direct arc (a shortest hub path whenever C
+ * satisfies the triangle inequality, e.g. Euclidean C).
+ *
+ * Chromosome encoding (§4.1): the p open hubs (node ids 0..n-1) and the
+ * allocation S, S[i] = the hub serving node i, S[k] = k for every hub k.
+ *
+ * Conventions.
+ *  - All matrices are row-major, node ids are 0-based.
+ *  - Functions return 0 (USAPHMP_OK) or a negative USAPHMP_E* code; the
+ *    message of the last failure of the calling thread is returned by
+ *    usaphmp_last_error().
+ *  - Host-pointer functions copy their inputs before returning and never keep
+ *    caller pointers.  *_dev functions take device pointers and a
+ *    cudaStream_t (passed as void*; NULL = the legacy default stream) and are
+ *    ordered on that stream; they return after enqueueing unless stated.
+ *  - A handle is not thread-safe: calls on one handle must not overlap.
+ *  - The library needs an sm_103 GPU; there is no CPU fallback.
+ */
+#ifndef USAPHMP_H
+#define USAPHMP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  USAPHMP_OK = 0,
+  USAPHMP_EINVAL = -1,        /* bad argument: size, null pointer, NaN/Inf/negative W or C */
+  USAPHMP_EINVAL_CHROM = -2,  /* a chromosome violates eq. (2), (3) or (5) */
+  USAPHMP_ENOMEM = -3,        /* device allocation failed */
+  USAPHMP_ECUDA = -4,         /* a CUDA call failed (message names it) */
+  USAPHMP_ETIMEOUT = -5,      /* a device-side wait gave up (kernel returned early) */
+  USAPHMP_EBUSY = -6          /* resource limit reached (admission refused) */
+};
+
+/* Evaluators of the transfer term. */
+enum {
+  USAPHMP_PATH_PLAIN_FP32 = 0,  /* fp32 CUDA cores, shared-memory gather of C[h(i)][h(j)] */
+  USAPHMP_PATH_SPLIT_BF16 = 1   /* tcgen05 GEMM W*A with W = bf16 hi + lo, fp32 accumulation */
+};
+
+typedef struct usaphmp_s* usaphmp_t;
+
+/* GA parameters (§5 names R islands of size n, N1 inner and N2 outer
+ * iterations without values; these are the library's choices). */
+typedef struct {
+  int32_t islands;      /* R >= 1 (default 64) */
+  int32_t island_size;  /* P, even, >= 2 (default 64); population B = R*P */
+  int32_t n1;           /* generations between island merges (default 10) */
+  int32_t path;         /* USAPHMP_PATH_* (default SPLIT_BF16) */
+  int32_t elitist;      /* 0 (default): ancestor = best child unconditionally */
+  int32_t use_graph;    /* 1 (default): replay generations from a CUDA graph */
+} usaphmp_params;
+
+typedef struct {
+  int32_t* hubs;      /* out [p], caller-allocated: best hubs, ascending */
+  int32_t* S;         /* out [n], caller-allocated: their nearest allocation */
+  double cost_fp64;   /* objective of (hubs, S) rescored in fp64 */
+  float cost_fp32;    /* the fast path's fitness of the same solution */
+  int64_t evals;      /* chromosome evaluations performed */
+  double ms;          /* wall time of the call */
+} usaphmp_result;
+
+/* Creates an instance: copies W and C (host, n*n floats each) to the device,
+ * checks them (finite, >= 0), computes O, D, the bf16 split of W and whether
+ * C is symmetric.  2 <= n <= 16384, 1 <= p <= min(n, 255).  Defines: §3. */
+int usaphmp_create(int32_t n, int32_t p, const float* W, const float* C, double chi,
+                   double alpha, double delta, usaphmp_t* out);
+
+/* Same with device W and C (n*n floats, row-major), read on `stream`; the
+ * call synchronises `stream` before returning. */
+int usaphmp_create_dev(int32_t n, int32_t p, const float* W, const float* C, double chi,
+                       double alpha, double delta, void* stream, usaphmp_t* out);
+
+int usaphmp_set_params(usaphmp_t h, const usaphmp_params* prm);
+int usaphmp_get_params(usaphmp_t h, usaphmp_params* prm);
+
+/* Fitness (objective 1, raw, unscaled) of B chromosomes given on the host:
+ * hubs [B][p] node ids (any order), S [B][n] node ids; fitness [B] out.
+ * Computed on the GPU by the configured path (fp32 arithmetic).  Returns
+ * USAPHMP_EINVAL_CHROM naming the first invalid chromosome. */
+int usaphmp_eval(usaphmp_t h, int32_t B, const int32_t* hubs, const int32_t* S, double* fitness);
+
+/* Same with device arrays; fitness is fp32 [B].  Validation needs the device
+ * status word, so this call synchronises `stream` before returning. */
+int usaphmp_eval_dev(usaphmp_t h, int32_t B, const int32_t* hubs, const int32_t* S,
+                     float* fitness, void* stream);
+
+/* Runs the GA (§5): middle-node initial solution (§4.1), `generations`
+ * generations of offspring + nearest allocation + evaluation + selection on
+ * the device, then fp64 rescoring of the best-ever solution. */
+int usaphmp_solve(usaphmp_t h, int32_t generations, uint64_t seed, usaphmp_result* best);
+
+void usaphmp_destroy(usaphmp_t h);
+const char* usaphmp_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * Step-level entry points on the library's internal layouts (device pointers,
+ * ordered on `stream`, no synchronisation, no validation).
+ *   mask  u32 [B][nw]  bit i%32 of word i/32 set <=> node i is a hub
+ *   hubs  i32 [B][p]   open hubs in ascending node order
+ *   slot  u8  [B][ns]  rank in `hubs` of the hub serving node i (ns >= n;
+ *                      bytes n..ns-1 are padding, written as 0xFF)
+ * ------------------------------------------------------------------------- */
+int usaphmp_layout(usaphmp_t h, int32_t* ns, int32_t* nw);
+
+/* Middle-node initial solution (§4.1): the p nodes with the smallest
+ * sum_j C[i][j] (lower id on ties).  mask [nw], hubs [p] out. */
+int usaphmp_initial_dev(usaphmp_t h, uint32_t* mask, int32_t* hubs, void* stream);
+
+/* Offspring of generation g for R islands of P members (§4.1, §4.2, §5):
+ * exchange, crossover, mutation, correction, driven by Philox4x32-10 draw
+ * streams of `seed`.  anc [R][nw] in; mask [R*P][nw] and hubs [R*P][p] out. */
+int usaphmp_children_dev(usaphmp_t h, int32_t R, int32_t P, const uint32_t* anc, uint64_t seed,
+                         int32_t g, uint32_t* mask, int32_t* hubs, void* stream);
+
+/* Nearest-hub allocation (§4.1, §5): slot [B][ns] out from ascending hubs. */
+int usaphmp_allocate_dev(usaphmp_t h, int32_t B, const int32_t* hubs, uint8_t* slot, void* stream);
+
+/* Fitness (fp32 [B] out) of chromosomes in canonical form (ascending hubs,
+ * slot codes) by the configured path.  Uses the handle's scratch buffers. */
+int usaphmp_eval_slots_dev(usaphmp_t h, int32_t B, const int32_t* hubs, const uint8_t* slot,
+                           float* fitness, void* stream);
+
+/* Selection of generation g (§5) for R islands of P members: ancestors
+ * anc [R][nw] / anc_fit [R], best-ever best [nw] / best_fit [1] updated in
+ * place from the children mask [R*P][nw] and their fitness [R*P]. */
+int usaphmp_select_dev(usaphmp_t h, int32_t R, int32_t P, int32_t g, const uint32_t* mask,
+                       const float* fitness, uint32_t* anc, float* anc_fit, uint32_t* best,
+                       float* best_fit, void* stream);
+
+/* FP64 objective (pair form of eq. 1) of B canonical chromosomes: cost [B]. */
+int usaphmp_rescore_fp64_dev(usaphmp_t h, int32_t B, const int32_t* hubs, const uint8_t* slot,
+                             double* cost, void* stream);
+
+/* GA run control (what usaphmp_solve does, split for timing):
+ * begin = initial solution + state; run = `generations` generations enqueued
+ * on `stream` without host synchronisation; result = rescoring + copy-out. */
+int usaphmp_ga_begin(usaphmp_t h, uint64_t seed, void* stream);
+int usaphmp_ga_run(usaphmp_t h, int32_t generations, void* stream);
+int usaphmp_ga_result(usaphmp_t h, usaphmp_result* best, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* USAPHMP_H */

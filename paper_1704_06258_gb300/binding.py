@@ -1,0 +1,207 @@
+"""ctypes binding of libusaphmp.so (argument marshalling only).
+
+Every function here forwards to the C ABI declared in include/usaphmp.h; the
+arithmetic runs in the library's CUDA kernels.  Device pointers are plain
+integers (e.g. ``torch.Tensor.data_ptr()``) and streams are raw
+``cudaStream_t`` values (e.g. ``torch.cuda.current_stream().cuda_stream``).
+There is no CPU fallback: without the built library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libusaphmp.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "usaphmp.h")
+
+PATH_PLAIN_FP32 = 0
+PATH_SPLIT_BF16 = 1
+
+ERRORS = {-1: "EINVAL", -2: "EINVAL_CHROM", -3: "ENOMEM", -4: "ECUDA", -5: "ETIMEOUT", -6: "EBUSY"}
+
+c_i32, c_i64, c_u64, c_f64, c_f32, c_vp = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                                           ctypes.c_double, ctypes.c_float, ctypes.c_void_p)
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("islands", c_i32), ("island_size", c_i32), ("n1", c_i32), ("path", c_i32),
+                ("elitist", c_i32), ("use_graph", c_i32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("hubs", ctypes.POINTER(c_i32)), ("S", ctypes.POINTER(c_i32)), ("cost_fp64", c_f64),
+                ("cost_fp32", c_f32), ("evals", c_i64), ("ms", c_f64)]
+
+
+class UsaphmpError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = ERRORS.get(code, str(code))
+
+
+_SIGS = {
+    "usaphmp_create": (c_i32, [c_i32, c_i32, c_vp, c_vp, c_f64, c_f64, c_f64, ctypes.POINTER(c_vp)]),
+    "usaphmp_create_dev": (c_i32, [c_i32, c_i32, c_vp, c_vp, c_f64, c_f64, c_f64, c_vp, ctypes.POINTER(c_vp)]),
+    "usaphmp_set_params": (c_i32, [c_vp, ctypes.POINTER(Params)]),
+    "usaphmp_get_params": (c_i32, [c_vp, ctypes.POINTER(Params)]),
+    "usaphmp_eval": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp]),
+    "usaphmp_eval_dev": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp, c_vp]),
+    "usaphmp_solve": (c_i32, [c_vp, c_i32, c_u64, ctypes.POINTER(Result)]),
+    "usaphmp_destroy": (None, [c_vp]),
+    "usaphmp_last_error": (ctypes.c_char_p, []),
+    "usaphmp_layout": (c_i32, [c_vp, ctypes.POINTER(c_i32), ctypes.POINTER(c_i32)]),
+    "usaphmp_initial_dev": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
+    "usaphmp_children_dev": (c_i32, [c_vp, c_i32, c_i32, c_vp, c_u64, c_i32, c_vp, c_vp, c_vp]),
+    "usaphmp_allocate_dev": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp]),
+    "usaphmp_eval_slots_dev": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp, c_vp]),
+    "usaphmp_select_dev": (c_i32, [c_vp, c_i32, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "usaphmp_rescore_fp64_dev": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_vp, c_vp]),
+    "usaphmp_ga_begin": (c_i32, [c_vp, c_u64, c_vp]),
+    "usaphmp_ga_run": (c_i32, [c_vp, c_i32, c_vp]),
+    "usaphmp_ga_result": (c_i32, [c_vp, ctypes.POINTER(Result), c_vp]),
+}
+
+_lib = None
+
+
+def header_functions(path=HEADER):
+    """Names of the functions declared in a public header."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(usaphmp_\w+)\s*\(", text)))
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(rc):
+    if rc != 0:
+        raise UsaphmpError(rc, (lib().usaphmp_last_error() or b"").decode())
+
+
+def _ptr(a):
+    return a.ctypes.data_as(c_vp)
+
+
+class Instance:
+    """One USApHMP instance resident on the GPU (a ``usaphmp_t``)."""
+
+    def __init__(self, W, C, p, chi=3.0, alpha=0.75, delta=2.0):
+        W = np.ascontiguousarray(W, dtype=np.float32)
+        C = np.ascontiguousarray(C, dtype=np.float32)
+        if W.ndim != 2 or W.shape[0] != W.shape[1] or C.shape != W.shape:
+            raise ValueError("W and C must be n x n")
+        self.n, self.p = int(W.shape[0]), int(p)
+        self.chi, self.alpha, self.delta = float(chi), float(alpha), float(delta)
+        h = c_vp()
+        check(lib().usaphmp_create(self.n, self.p, _ptr(W), _ptr(C), self.chi, self.alpha, self.delta,
+                                   ctypes.byref(h)))
+        self.h = h
+        ns, nw = c_i32(), c_i32()
+        check(lib().usaphmp_layout(self.h, ctypes.byref(ns), ctypes.byref(nw)))
+        self.ns, self.nw = ns.value, nw.value
+
+    @classmethod
+    def from_instance(cls, inst):
+        return cls(inst.W, inst.C, inst.p, inst.chi, inst.alpha, inst.delta)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().usaphmp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # parameters
+    @property
+    def params(self):
+        prm = Params()
+        check(lib().usaphmp_get_params(self.h, ctypes.byref(prm)))
+        return {f: getattr(prm, f) for f, _ in Params._fields_}
+
+    def set_params(self, **kw):
+        cur = self.params
+        cur.update(kw)
+        prm = Params(**cur)
+        check(lib().usaphmp_set_params(self.h, ctypes.byref(prm)))
+
+    # public calls
+    def eval(self, hubs, S):
+        hubs = np.ascontiguousarray(hubs, dtype=np.int32)
+        S = np.ascontiguousarray(S, dtype=np.int32)
+        B = hubs.shape[0]
+        if hubs.shape != (B, self.p) or S.shape != (B, self.n):
+            raise ValueError("hubs must be [B, p] and S [B, n]")
+        out = np.empty(B, dtype=np.float64)
+        check(lib().usaphmp_eval(self.h, B, _ptr(hubs), _ptr(S), _ptr(out)))
+        return out
+
+    def eval_dev(self, B, hubs_ptr, S_ptr, fitness_ptr, stream=0):
+        check(lib().usaphmp_eval_dev(self.h, B, hubs_ptr, S_ptr, fitness_ptr, stream))
+
+    def solve(self, generations, seed):
+        hubs = np.empty(self.p, dtype=np.int32)
+        S = np.empty(self.n, dtype=np.int32)
+        r = Result(hubs.ctypes.data_as(ctypes.POINTER(c_i32)), S.ctypes.data_as(ctypes.POINTER(c_i32)))
+        check(lib().usaphmp_solve(self.h, generations, seed, ctypes.byref(r)))
+        return {"hubs": hubs, "S": S, "cost_fp64": r.cost_fp64, "cost_fp32": r.cost_fp32,
+                "evals": r.evals, "ms": r.ms}
+
+    # step-level calls (device pointers)
+    def initial_dev(self, mask_ptr, hubs_ptr, stream=0):
+        check(lib().usaphmp_initial_dev(self.h, mask_ptr, hubs_ptr, stream))
+
+    def children_dev(self, R, P, anc_ptr, seed, g, mask_ptr, hubs_ptr, stream=0):
+        check(lib().usaphmp_children_dev(self.h, R, P, anc_ptr, seed, g, mask_ptr, hubs_ptr, stream))
+
+    def allocate_dev(self, B, hubs_ptr, slot_ptr, stream=0):
+        check(lib().usaphmp_allocate_dev(self.h, B, hubs_ptr, slot_ptr, stream))
+
+    def eval_slots_dev(self, B, hubs_ptr, slot_ptr, fitness_ptr, stream=0):
+        check(lib().usaphmp_eval_slots_dev(self.h, B, hubs_ptr, slot_ptr, fitness_ptr, stream))
+
+    def select_dev(self, R, P, g, mask_ptr, fit_ptr, anc_ptr, anc_fit_ptr, best_ptr, best_fit_ptr, stream=0):
+        check(lib().usaphmp_select_dev(self.h, R, P, g, mask_ptr, fit_ptr, anc_ptr, anc_fit_ptr, best_ptr,
+                                       best_fit_ptr, stream))
+
+    def rescore_fp64_dev(self, B, hubs_ptr, slot_ptr, cost_ptr, stream=0):
+        check(lib().usaphmp_rescore_fp64_dev(self.h, B, hubs_ptr, slot_ptr, cost_ptr, stream))
+
+    def ga_begin(self, seed, stream=0):
+        check(lib().usaphmp_ga_begin(self.h, seed, stream))
+
+    def ga_run(self, generations, stream=0):
+        check(lib().usaphmp_ga_run(self.h, generations, stream))
+
+    def ga_result(self, stream=0):
+        hubs = np.empty(self.p, dtype=np.int32)
+        S = np.empty(self.n, dtype=np.int32)
+        r = Result(hubs.ctypes.data_as(ctypes.POINTER(c_i32)), S.ctypes.data_as(ctypes.POINTER(c_i32)))
+        check(lib().usaphmp_ga_result(self.h, ctypes.byref(r), stream))
+        return {"hubs": hubs, "S": S, "cost_fp64": r.cost_fp64, "cost_fp32": r.cost_fp32, "evals": r.evals}

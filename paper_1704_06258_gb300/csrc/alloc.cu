@@ -1,0 +1,88 @@
+// Nearest-hub allocation (§4.1; checked after every operator in §5) and the
+// access terms of objective (1), §3:
+//   slot_b(i) = argmin_l C[i, hubs_b[l]]   (lowest node id on ties; a hub
+//               serves itself),
+//   t12_b     = sum_i chi*O_i*C[i,h(i)] + delta*D_i*C[h(i),i],
+// plus, for the tensor-core evaluator, chubT_b[l][k] = C[hubs_b[k], hubs_b[l]].
+// One block per chromosome; C[i, hub] is read as CT[hub][i], so the p loads
+// of each node are coalesced across the block.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace usaphmp {
+
+template <bool kNearest>
+__global__ void __launch_bounds__(256) k_alloc(const __grid_constant__ TaskParam tp, int with_chub) {
+  __shared__ int hs[kMaxP];
+  __shared__ float red[32];
+  const int t = task_of(tp.bo, blockIdx.x);
+  const Task& T = task_at(tp, t);
+  const int b = blockIdx.x - tp.bo.o[t];
+  const int n = T.in.n, p = T.in.p, ldw = T.in.ldw, ns = T.in.ns;
+  const float* __restrict__ C = T.in.C;
+  const float* __restrict__ CT = T.in.CT;
+  const float* __restrict__ O = T.in.O;
+  const float* __restrict__ D = T.in.D;
+  const float chi = T.in.chi, delta = T.in.delta;
+  const bool sym = T.in.symmetric != 0;
+  uint8_t* __restrict__ slot = T.pop.slot + (long long)b * ns;
+  const uint8_t* __restrict__ slot_in = T.pop.slot_in ? T.pop.slot_in + (long long)b * ns : slot;
+  bool bad = false;
+  for (int k = threadIdx.x; k < p; k += blockDim.x) {
+    int v = T.pop.hubs_in ? T.pop.hubs_in[(long long)b * p + k] : T.pop.hubs[(long long)b * p + k];
+    if (v < 0 || v >= n) { bad = true; v = 0; }
+    hs[k] = v;
+    if (T.pop.hubs_in) T.pop.hubs[(long long)b * p + k] = v;
+  }
+  __syncthreads();
+
+  float acc = 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    int bl;
+    float cih;  // C[i, h(i)]
+    if (kNearest) {
+      bl = 0;
+      cih = CT[(long long)hs[0] * ldw + i];
+      int own = (hs[0] == i) ? 0 : -1;
+      for (int l = 1; l < p; ++l) {
+        const int hl = hs[l];
+        const float v = CT[(long long)hl * ldw + i];
+        if (v < cih) { cih = v; bl = l; }
+        if (hl == i) own = l;
+      }
+      if (own >= 0) { bl = own; cih = CT[(long long)i * ldw + i]; }
+      slot[i] = (uint8_t)bl;
+    } else {
+      bl = slot_in[i];
+      if (bl >= p) { bad = true; bl = 0; }
+      slot[i] = (uint8_t)bl;
+      cih = CT[(long long)hs[bl] * ldw + i];
+    }
+    const float chi_i = sym ? cih : C[(long long)hs[bl] * ldw + i];  // C[h(i), i]
+    acc += chi * O[i] * cih + delta * D[i] * chi_i;
+  }
+  for (int i = n + threadIdx.x; i < ns; i += blockDim.x) slot[i] = kSlotPad;
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(T.pop.status, kStatusBadChromosome);
+  const float s = block_sum(acc, red);
+  if (threadIdx.x == 0) T.pop.t12[b] = s;
+  if (with_chub) {
+    float* __restrict__ ch = T.pop.chubT + (long long)b * p * p;
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+      const int l = e / p, k = e - l * p;
+      ch[e] = C[(long long)hs[k] * ldw + hs[l]];
+    }
+  }
+}
+
+void launch_alloc(const TaskSet& ts, bool nearest, bool with_chub, cudaStream_t s) {
+  TaskParam tp = make_param(ts);
+  for (int t = 0; t < ts.count; ++t) tp.bo.o[t + 1] = tp.bo.o[t] + ts.h[t].pop.B;
+  const int blocks = tp.bo.o[ts.count];
+  if (blocks == 0) return;
+  if (nearest)
+    k_alloc<true><<<blocks, 256, 0, s>>>(tp, with_chub ? 1 : 0);
+  else
+    k_alloc<false><<<blocks, 256, 0, s>>>(tp, with_chub ? 1 : 0);
+}
+
+}  // namespace usaphmp

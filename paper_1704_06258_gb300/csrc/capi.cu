@@ -1,0 +1,684 @@
+// C ABI and host engine: instance set-up, workspaces, the evaluation
+// pipeline (canonical form -> allocation / access terms -> transfer term ->
+// fixed-order reduction) and the GA driver (§5) with CUDA-graph replay of
+// generations.  Every arithmetic step runs in the library's kernels.
+#include "usaphmp.h"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+using namespace usaphmp;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  cudaGetLastError();
+  return fail(e == cudaErrorMemoryAllocation ? USAPHMP_ENOMEM : USAPHMP_ECUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(x)                                                   \
+  do {                                                          \
+    cudaError_t e_ = (x);                                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #x);            \
+  } while (0)
+
+#define RET(x)                  \
+  do {                          \
+    int r_ = (x);               \
+    if (r_ != USAPHMP_OK) return r_; \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * std::max<size_t>(count, 1));
+}
+
+template <class T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+// Device buffers of a population of up to `cap` chromosomes.
+struct Pop {
+  int cap = 0;
+  size_t part_cap = 0;
+  uint32_t* mask = nullptr;
+  int32_t* hubs = nullptr;
+  uint8_t* slot = nullptr;
+  float* t12 = nullptr;
+  float* chubT = nullptr;
+  float* part = nullptr;
+  float* fit = nullptr;
+  void release() {
+    dfree(mask); dfree(hubs); dfree(slot); dfree(t12); dfree(chubT); dfree(part); dfree(fit);
+    cap = 0;
+    part_cap = 0;
+  }
+};
+
+}  // namespace
+
+struct usaphmp_s {
+  int n = 0, p = 0, ldw = 0, ns = 0, nw = 0;
+  double chi = 0, alpha = 0, delta = 0;
+  int symmetric = 0;
+  float* W = nullptr;
+  float* C = nullptr;
+  float* CTbuf = nullptr;
+  float* O = nullptr;
+  float* D = nullptr;
+  __nv_bfloat16* Whi = nullptr;
+  __nv_bfloat16* Wlo = nullptr;
+  void* tmaps = nullptr;  // two CUtensorMap in device memory
+  usaphmp_params prm{};
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  uint32_t* d_status = nullptr;
+  int* d_bad = nullptr;
+  uint32_t* h_status = nullptr;  // pinned
+  int* h_bad = nullptr;          // pinned
+  double* d_dscratch = nullptr;
+  double* d_cost = nullptr;
+  double* d_rpart = nullptr;
+  int rpart_cap = 0;
+  // evaluation workspace and host-call staging
+  Pop ev;
+  int32_t* d_hubs_in = nullptr;
+  int32_t* d_S_in = nullptr;
+  float* d_fit_out = nullptr;
+  int in_cap = 0;
+  // GA
+  Pop ga;
+  Pop one;
+  int ga_R = 0, ga_P = 0;
+  uint32_t* anc = nullptr;
+  float* anc_fit = nullptr;
+  uint32_t* best = nullptr;
+  float* best_fit = nullptr;
+  int* gen = nullptr;
+  uint32_t* mask0 = nullptr;
+  Task ga_task{};
+  bool ga_ready = false;
+  int64_t ga_evals = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t graph_stream = nullptr;
+};
+
+namespace {
+
+DevInst inst_of(const usaphmp_s* h) {
+  DevInst in;
+  in.n = h->n; in.p = h->p; in.ldw = h->ldw; in.ns = h->ns; in.nw = h->nw;
+  in.symmetric = h->symmetric;
+  in.chi = (float)h->chi; in.alpha = (float)h->alpha; in.delta = (float)h->delta;
+  in.W = h->W; in.C = h->C; in.CT = h->symmetric ? h->C : h->CTbuf;
+  in.O = h->O; in.D = h->D; in.Whi = h->Whi; in.Wlo = h->Wlo;
+  return in;
+}
+
+bool use_tc(const usaphmp_s* h) { return h->prm.path == USAPHMP_PATH_SPLIT_BF16; }
+
+int part_rows(const usaphmp_s* h, int B) {
+  return use_tc(h) ? (h->n + tc_tile_rows() - 1) / tc_tile_rows() : plain_rows(h->n, B);
+}
+
+size_t part_elems(const usaphmp_s* h, int B) {
+  const size_t tc = (size_t)((h->n + tc_tile_rows() - 1) / tc_tile_rows()) * B * h->p;
+  const size_t plain = (size_t)plain_rows(h->n, B) * B;
+  return std::max(tc, plain);
+}
+
+int ensure_pop(usaphmp_s* h, Pop& P, int B) {
+  const size_t need_part = part_elems(h, B);
+  if (P.cap >= B && P.part_cap >= need_part) return USAPHMP_OK;
+  P.release();
+  CK(dalloc(&P.mask, (size_t)B * h->nw));
+  CK(dalloc(&P.hubs, (size_t)B * h->p));
+  CK(dalloc(&P.slot, (size_t)B * h->ns));
+  CK(dalloc(&P.t12, (size_t)B));
+  CK(dalloc(&P.chubT, (size_t)B * h->p * h->p));
+  CK(dalloc(&P.part, need_part));
+  CK(dalloc(&P.fit, (size_t)B));
+  P.cap = B;
+  P.part_cap = need_part;
+  return USAPHMP_OK;
+}
+
+PopBuf popbuf(const usaphmp_s* h, const Pop& P, int B) {
+  PopBuf pb;
+  pb.B = B;
+  pb.mask = P.mask; pb.hubs = P.hubs; pb.slot = P.slot; pb.t12 = P.t12;
+  pb.chubT = P.chubT; pb.part = P.part; pb.fit = P.fit;
+  pb.npart = part_rows(h, B);
+  pb.part_width = use_tc(h) ? h->p : 1;
+  pb.hubs_in = nullptr;
+  pb.slot_in = nullptr;
+  pb.status = h->d_status;
+  return pb;
+}
+
+Task make_task(const usaphmp_s* h, const PopBuf& pb) {
+  Task t{};
+  t.in = inst_of(h);
+  t.pop = pb;
+  t.tmap_hi = h->tmaps;
+  t.tmap_lo = h->tmaps ? static_cast<const char*>(h->tmaps) + sizeof(CUtensorMap) : nullptr;
+  return t;
+}
+
+int check_status(usaphmp_s* h, cudaStream_t s, const char* what) {
+  CK(cudaMemcpyAsync(h->h_status, h->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h->h_bad, h->d_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const uint32_t st = *h->h_status;
+  if (st & kStatusTimeout) return fail(USAPHMP_ETIMEOUT, std::string(what) + ": a device wait timed out");
+  if (st & kStatusBadChromosome)
+    return fail(USAPHMP_EINVAL_CHROM, std::string(what) + ": chromosome " + std::to_string(*h->h_bad) +
+                                          " is not a valid single allocation (distinct hubs, S[i] an open hub, S[hub] = hub)");
+  if (st & kStatusBadValue) return fail(USAPHMP_EINVAL, std::string(what) + ": W or C has a negative or non-finite entry");
+  return USAPHMP_OK;
+}
+
+int reset_status(usaphmp_s* h, cudaStream_t s) {
+  CK(cudaMemsetAsync(h->d_status, 0, sizeof(uint32_t), s));
+  CK(cudaMemsetAsync(h->d_bad, 0x7f, sizeof(int), s));
+  return USAPHMP_OK;
+}
+
+// Transfer term + reduction for a task whose hubs/slots/t12/chubT are set.
+int run_transfer(usaphmp_s* h, const Task& task, cudaStream_t s) {
+  TaskSet ts{nullptr, &task, 1};
+  if (use_tc(h))
+    launch_eval_tc(ts, h->num_sms, h->d_status, s);
+  else
+    launch_eval_plain(ts, s);
+  CK(cudaGetLastError());
+  launch_reduce(ts, s);
+  CK(cudaGetLastError());
+  return USAPHMP_OK;
+}
+
+// Allocation (nearest or given), access terms, transfer term, reduction.
+int run_eval(usaphmp_s* h, const Task& task, bool nearest, cudaStream_t s) {
+  TaskSet ts{nullptr, &task, 1};
+  launch_alloc(ts, nearest, use_tc(h), s);
+  CK(cudaGetLastError());
+  return run_transfer(h, task, s);
+}
+
+int encode_tmaps(usaphmp_s* h) {
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+  if (!fn || q != cudaDriverEntryPointSuccess) return fail(USAPHMP_ECUDA, "cuTensorMapEncodeTiled not available");
+  auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  CUtensorMap maps[2];
+  for (int k = 0; k < 2; ++k) {
+    const cuuint64_t dims[2] = {(cuuint64_t)h->ldw, (cuuint64_t)h->n};
+    const cuuint64_t strides[1] = {(cuuint64_t)h->ldw * 2};
+    const cuuint32_t box[2] = {64, 128};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(&maps[k], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, k == 0 ? (void*)h->Whi : (void*)h->Wlo,
+                        dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(USAPHMP_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  }
+  CK(cudaMalloc(&h->tmaps, sizeof(maps)));
+  CK(cudaMemcpy(h->tmaps, maps, sizeof(maps), cudaMemcpyHostToDevice));
+  return USAPHMP_OK;
+}
+
+int create_common(usaphmp_s* h, const float* W, const float* C, bool dev, cudaStream_t s) {
+  const int n = h->n;
+  CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+  int dev_id = 0;
+  CK(cudaGetDevice(&dev_id));
+  CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev_id));
+  int optin = 0;
+  CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev_id));
+  prepare_eval_plain(optin);
+  prepare_eval_tc();
+  CK(cudaGetLastError());
+  const size_t mat = (size_t)n * h->ldw;
+  CK(dalloc(&h->W, mat));
+  CK(dalloc(&h->C, mat));
+  CK(dalloc(&h->O, n));
+  CK(dalloc(&h->D, n));
+  CK(dalloc(&h->Whi, mat));
+  CK(dalloc(&h->Wlo, mat));
+  CK(dalloc(&h->d_status, 1));
+  CK(dalloc(&h->d_bad, 1));
+  CK(dalloc(&h->d_dscratch, n));
+  CK(cudaMallocHost(&h->h_status, sizeof(uint32_t)));
+  CK(cudaMallocHost(&h->h_bad, sizeof(int)));
+  if (!dev) s = h->stream;
+  CK(cudaMemsetAsync(h->W, 0, mat * sizeof(float), s));
+  CK(cudaMemsetAsync(h->C, 0, mat * sizeof(float), s));
+  const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpy2DAsync(h->W, h->ldw * sizeof(float), W, n * sizeof(float), n * sizeof(float), n, kind, s));
+  CK(cudaMemcpy2DAsync(h->C, h->ldw * sizeof(float), C, n * sizeof(float), n * sizeof(float), n, kind, s));
+  RET(reset_status(h, s));
+  launch_check_values(h->W, h->C, n, h->ldw, h->d_status, s);
+  launch_split_bf16(h->W, h->Whi, h->Wlo, (long long)mat, s);
+  launch_flows(h->W, n, h->ldw, h->O, h->D, s);
+  uint32_t* d_asym = reinterpret_cast<uint32_t*>(h->d_bad);  // reuse as a flag
+  CK(cudaMemsetAsync(d_asym, 0, sizeof(uint32_t), s));
+  launch_asymmetry(h->C, n, h->ldw, d_asym, s);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(h->h_bad, d_asym, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h->h_status, h->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (*h->h_status & kStatusBadValue) return fail(USAPHMP_EINVAL, "W or C has a negative or non-finite entry");
+  h->symmetric = (*h->h_bad == 0) ? 1 : 0;
+  if (!h->symmetric) {
+    CK(dalloc(&h->CTbuf, mat));
+    CK(cudaMemsetAsync(h->CTbuf, 0, mat * sizeof(float), s));
+    launch_transpose(h->C, h->CTbuf, n, h->ldw, s);
+    CK(cudaGetLastError());
+  }
+  RET(encode_tmaps(h));
+  CK(cudaStreamSynchronize(s));
+  return USAPHMP_OK;
+}
+
+int create_impl(int32_t n, int32_t p, const float* W, const float* C, double chi, double alpha, double delta,
+                bool dev, void* stream, usaphmp_t* out) {
+  if (!out) return fail(USAPHMP_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!W || !C) return fail(USAPHMP_EINVAL, "W or C is NULL");
+  if (n < 2 || n > kMaxN) return fail(USAPHMP_EINVAL, "n must be in [2, 16384]");
+  if (p < 1 || p > n || p > kMaxP) return fail(USAPHMP_EINVAL, "p must be in [1, min(n, 255)]");
+  if (!(chi >= 0) || !(alpha >= 0) || !(delta >= 0) || chi > 1e30 || alpha > 1e30 || delta > 1e30)
+    return fail(USAPHMP_EINVAL, "chi, alpha, delta must be finite and >= 0");
+  usaphmp_s* h = new usaphmp_s();
+  h->n = n; h->p = p;
+  h->ldw = round_up(n, 8);
+  h->ns = round_up(n, 64);
+  h->nw = (n + 31) / 32;
+  h->chi = chi; h->alpha = alpha; h->delta = delta;
+  h->prm.islands = 64;
+  h->prm.island_size = 64;
+  h->prm.n1 = 10;
+  h->prm.path = USAPHMP_PATH_SPLIT_BF16;
+  h->prm.elitist = 0;
+  h->prm.use_graph = 1;
+  const int r = create_common(h, W, C, dev, static_cast<cudaStream_t>(stream));
+  if (r != USAPHMP_OK) {
+    const std::string msg = g_err;
+    usaphmp_destroy(h);
+    g_err = msg;
+    return r;
+  }
+  *out = h;
+  return USAPHMP_OK;
+}
+
+void drop_graph(usaphmp_s* h) {
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->gexec = nullptr;
+  h->graph = nullptr;
+}
+
+int eval_canonical(usaphmp_s* h, int B, const int32_t* hubs_in, const int32_t* S, float* fit_out, cudaStream_t s) {
+  RET(ensure_pop(h, h->ev, B));
+  RET(reset_status(h, s));
+  launch_canon(hubs_in, S, B, h->n, h->p, h->ns, h->ev.hubs, h->ev.slot, h->d_status, h->d_bad, s);
+  CK(cudaGetLastError());
+  PopBuf pb = popbuf(h, h->ev, B);
+  pb.fit = fit_out;
+  const Task task = make_task(h, pb);
+  RET(run_eval(h, task, false, s));
+  return check_status(h, s, "usaphmp_eval");
+}
+
+// GA state for R islands of P (B = R*P); (re)allocated when the shape changes.
+int ensure_ga(usaphmp_s* h) {
+  const int R = h->prm.islands, P = h->prm.island_size, B = R * P;
+  RET(ensure_pop(h, h->ga, B));
+  RET(ensure_pop(h, h->one, 1));
+  if (h->ga_R != R || h->ga_P != P || !h->anc) {
+    dfree(h->anc); dfree(h->anc_fit); dfree(h->best); dfree(h->best_fit); dfree(h->gen); dfree(h->mask0);
+    CK(dalloc(&h->anc, (size_t)R * h->nw));
+    CK(dalloc(&h->anc_fit, (size_t)R));
+    CK(dalloc(&h->best, (size_t)h->nw));
+    CK(dalloc(&h->best_fit, 1));
+    CK(dalloc(&h->gen, 1));
+    CK(dalloc(&h->mask0, (size_t)h->nw));
+    h->ga_R = R;
+    h->ga_P = P;
+  }
+  const int np = rescore_parts(h->n);
+  if (h->rpart_cap < np) {
+    dfree(h->d_rpart); dfree(h->d_cost);
+    CK(dalloc(&h->d_rpart, (size_t)np * 2));
+    CK(dalloc(&h->d_cost, 2));
+    h->rpart_cap = np;
+  }
+  return USAPHMP_OK;
+}
+
+Task ga_task_of(usaphmp_s* h, unsigned long long seed) {
+  const int R = h->prm.islands, P = h->prm.island_size;
+  Task t = make_task(h, popbuf(h, h->ga, R * P));
+  t.ga.R = R; t.ga.P = P; t.ga.N1 = h->prm.n1; t.ga.elitist = h->prm.elitist;
+  t.ga.seed = seed;
+  t.ga.gen = h->gen; t.ga.anc = h->anc; t.ga.anc_fit = h->anc_fit;
+  t.ga.best = h->best; t.ga.best_fit = h->best_fit;
+  return t;
+}
+
+int enqueue_generation(usaphmp_s* h, cudaStream_t s) {
+  TaskSet ts{nullptr, &h->ga_task, 1};
+  launch_children(ts, s);
+  CK(cudaGetLastError());
+  RET(run_eval(h, h->ga_task, true, s));
+  launch_select(ts, s);
+  CK(cudaGetLastError());
+  return USAPHMP_OK;
+}
+
+// Decodes a mask into ascending hubs on the host (tiny; result copy-out only).
+std::vector<int32_t> mask_to_hubs(const std::vector<uint32_t>& m, int n) {
+  std::vector<int32_t> hubs;
+  for (int i = 0; i < n; ++i)
+    if (m[i >> 5] & (1u << (i & 31))) hubs.push_back(i);
+  return hubs;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* usaphmp_last_error(void) { return g_err.c_str(); }
+
+int usaphmp_create(int32_t n, int32_t p, const float* W, const float* C, double chi, double alpha,
+                   double delta, usaphmp_t* out) {
+  return create_impl(n, p, W, C, chi, alpha, delta, false, nullptr, out);
+}
+
+int usaphmp_create_dev(int32_t n, int32_t p, const float* W, const float* C, double chi, double alpha,
+                       double delta, void* stream, usaphmp_t* out) {
+  return create_impl(n, p, W, C, chi, alpha, delta, true, stream, out);
+}
+
+void usaphmp_destroy(usaphmp_t h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  drop_graph(h);
+  if (h->graph_stream) cudaStreamDestroy(h->graph_stream);
+  dfree(h->W); dfree(h->C); dfree(h->CTbuf); dfree(h->O); dfree(h->D); dfree(h->Whi); dfree(h->Wlo);
+  if (h->tmaps) cudaFree(h->tmaps);
+  dfree(h->d_status); dfree(h->d_bad); dfree(h->d_dscratch); dfree(h->d_cost); dfree(h->d_rpart);
+  if (h->h_status) cudaFreeHost(h->h_status);
+  if (h->h_bad) cudaFreeHost(h->h_bad);
+  h->ev.release(); h->ga.release(); h->one.release();
+  dfree(h->d_hubs_in); dfree(h->d_S_in); dfree(h->d_fit_out);
+  dfree(h->anc); dfree(h->anc_fit); dfree(h->best); dfree(h->best_fit); dfree(h->gen); dfree(h->mask0);
+  if (h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+int usaphmp_set_params(usaphmp_t h, const usaphmp_params* prm) {
+  if (!h || !prm) return fail(USAPHMP_EINVAL, "NULL argument");
+  if (prm->islands < 1 || prm->island_size < 2 || (prm->island_size & 1))
+    return fail(USAPHMP_EINVAL, "islands must be >= 1 and island_size even and >= 2");
+  if ((long long)prm->islands * prm->island_size > (1 << 24)) return fail(USAPHMP_EINVAL, "population too large");
+  if (prm->n1 < 1) return fail(USAPHMP_EINVAL, "n1 must be >= 1");
+  if (prm->path != USAPHMP_PATH_PLAIN_FP32 && prm->path != USAPHMP_PATH_SPLIT_BF16)
+    return fail(USAPHMP_EINVAL, "unknown path");
+  h->prm = *prm;
+  h->ga_ready = false;
+  drop_graph(h);
+  return USAPHMP_OK;
+}
+
+int usaphmp_get_params(usaphmp_t h, usaphmp_params* prm) {
+  if (!h || !prm) return fail(USAPHMP_EINVAL, "NULL argument");
+  *prm = h->prm;
+  return USAPHMP_OK;
+}
+
+int usaphmp_eval_dev(usaphmp_t h, int32_t B, const int32_t* hubs, const int32_t* S, float* fitness, void* stream) {
+  if (!h) return fail(USAPHMP_EINVAL, "NULL handle");
+  if (B < 0) return fail(USAPHMP_EINVAL, "B < 0");
+  if (B == 0) return USAPHMP_OK;
+  if (!hubs || !S || !fitness) return fail(USAPHMP_EINVAL, "NULL argument");
+  return eval_canonical(h, B, hubs, S, fitness, static_cast<cudaStream_t>(stream));
+}
+
+int usaphmp_eval(usaphmp_t h, int32_t B, const int32_t* hubs, const int32_t* S, double* fitness) {
+  if (!h) return fail(USAPHMP_EINVAL, "NULL handle");
+  if (B < 0) return fail(USAPHMP_EINVAL, "B < 0");
+  if (B == 0) return USAPHMP_OK;
+  if (!hubs || !S || !fitness) return fail(USAPHMP_EINVAL, "NULL argument");
+  cudaStream_t s = h->stream;
+  if (h->in_cap < B) {
+    dfree(h->d_hubs_in); dfree(h->d_S_in); dfree(h->d_fit_out);
+    CK(dalloc(&h->d_hubs_in, (size_t)B * h->p));
+    CK(dalloc(&h->d_S_in, (size_t)B * h->n));
+    CK(dalloc(&h->d_fit_out, (size_t)B));
+    h->in_cap = B;
+  }
+  CK(cudaMemcpyAsync(h->d_hubs_in, hubs, sizeof(int32_t) * B * h->p, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->d_S_in, S, sizeof(int32_t) * B * h->n, cudaMemcpyHostToDevice, s));
+  RET(eval_canonical(h, B, h->d_hubs_in, h->d_S_in, h->d_fit_out, s));
+  std::vector<float> f(B);
+  CK(cudaMemcpyAsync(f.data(), h->d_fit_out, sizeof(float) * B, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int b = 0; b < B; ++b) fitness[b] = f[b];
+  return USAPHMP_OK;
+}
+
+int usaphmp_layout(usaphmp_t h, int32_t* ns, int32_t* nw) {
+  if (!h) return fail(USAPHMP_EINVAL, "NULL handle");
+  if (ns) *ns = h->ns;
+  if (nw) *nw = h->nw;
+  return USAPHMP_OK;
+}
+
+int usaphmp_initial_dev(usaphmp_t h, uint32_t* mask, int32_t* hubs, void* stream) {
+  if (!h || !mask || !hubs) return fail(USAPHMP_EINVAL, "NULL argument");
+  launch_middle_nodes(h->C, h->n, h->ldw, h->p, h->d_dscratch, mask, hubs, static_cast<cudaStream_t>(stream));
+  CK(cudaGetLastError());
+  return USAPHMP_OK;
+}
+
+int usaphmp_children_dev(usaphmp_t h, int32_t R, int32_t P, const uint32_t* anc, uint64_t seed, int32_t g,
+                         uint32_t* mask, int32_t* hubs, void* stream) {
+  if (!h || !anc || !mask || !hubs) return fail(USAPHMP_EINVAL, "NULL argument");
+  if (R < 1 || P < 2 || (P & 1) || g < 0) return fail(USAPHMP_EINVAL, "bad R, P or g");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  RET(ensure_ga(h));
+  Task t{};
+  t.in = inst_of(h);
+  t.pop.B = R * P;
+  t.pop.mask = mask;
+  t.pop.hubs = hubs;
+  t.ga.R = R; t.ga.P = P; t.ga.seed = seed;
+  t.ga.anc = const_cast<uint32_t*>(anc);
+  t.ga.gen = h->gen;
+  CK(cudaMemcpyAsync(h->gen, &g, sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));  // g lives on the host stack
+  TaskSet ts{nullptr, &t, 1};
+  launch_children(ts, s);
+  CK(cudaGetLastError());
+  return USAPHMP_OK;
+}
+
+int usaphmp_allocate_dev(usaphmp_t h, int32_t B, const int32_t* hubs, uint8_t* slot, void* stream) {
+  if (!h || !hubs || !slot) return fail(USAPHMP_EINVAL, "NULL argument");
+  if (B <= 0) return B == 0 ? USAPHMP_OK : fail(USAPHMP_EINVAL, "B < 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  RET(ensure_pop(h, h->ev, B));
+  PopBuf pb = popbuf(h, h->ev, B);
+  pb.hubs_in = hubs;
+  pb.slot = slot;
+  const Task t = make_task(h, pb);
+  TaskSet ts{nullptr, &t, 1};
+  launch_alloc(ts, true, false, s);
+  CK(cudaGetLastError());
+  return USAPHMP_OK;
+}
+
+int usaphmp_eval_slots_dev(usaphmp_t h, int32_t B, const int32_t* hubs, const uint8_t* slot, float* fitness,
+                           void* stream) {
+  if (!h || !hubs || !slot || !fitness) return fail(USAPHMP_EINVAL, "NULL argument");
+  if (B <= 0) return B == 0 ? USAPHMP_OK : fail(USAPHMP_EINVAL, "B < 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  RET(ensure_pop(h, h->ev, B));
+  PopBuf pb = popbuf(h, h->ev, B);
+  pb.hubs_in = hubs;
+  pb.slot_in = slot;
+  pb.fit = fitness;
+  const Task t = make_task(h, pb);
+  return run_eval(h, t, false, s);
+}
+
+int usaphmp_select_dev(usaphmp_t h, int32_t R, int32_t P, int32_t g, const uint32_t* mask, const float* fitness,
+                       uint32_t* anc, float* anc_fit, uint32_t* best, float* best_fit, void* stream) {
+  if (!h || !mask || !fitness || !anc || !anc_fit || !best || !best_fit) return fail(USAPHMP_EINVAL, "NULL argument");
+  if (R < 1 || P < 1 || g < 0) return fail(USAPHMP_EINVAL, "bad R, P or g");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  RET(ensure_ga(h));
+  Task t{};
+  t.in = inst_of(h);
+  t.pop.B = R * P;
+  t.pop.mask = const_cast<uint32_t*>(mask);
+  t.pop.fit = const_cast<float*>(fitness);
+  t.ga.R = R; t.ga.P = P; t.ga.N1 = h->prm.n1; t.ga.elitist = h->prm.elitist;
+  t.ga.anc = anc; t.ga.anc_fit = anc_fit; t.ga.best = best; t.ga.best_fit = best_fit;
+  t.ga.gen = h->gen;
+  CK(cudaMemcpyAsync(h->gen, &g, sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  TaskSet ts{nullptr, &t, 1};
+  launch_select(ts, s);
+  CK(cudaGetLastError());
+  return USAPHMP_OK;
+}
+
+int usaphmp_rescore_fp64_dev(usaphmp_t h, int32_t B, const int32_t* hubs, const uint8_t* slot, double* cost,
+                             void* stream) {
+  if (!h || !hubs || !slot || !cost) return fail(USAPHMP_EINVAL, "NULL argument");
+  if (B <= 0) return B == 0 ? USAPHMP_OK : fail(USAPHMP_EINVAL, "B < 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double* part = nullptr;
+  CK(dalloc(&part, (size_t)rescore_parts(h->n) * B));
+  launch_rescore(inst_of(h), B, hubs, slot, part, cost, s);
+  cudaError_t e = cudaGetLastError();
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  cudaFree(part);
+  CK(e);
+  CK(e2);
+  return USAPHMP_OK;
+}
+
+int usaphmp_ga_begin(usaphmp_t h, uint64_t seed, void* stream) {
+  if (!h) return fail(USAPHMP_EINVAL, "NULL handle");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  RET(ensure_ga(h));
+  drop_graph(h);
+  RET(reset_status(h, s));
+  // initial solution (§4.1) and its fitness
+  launch_middle_nodes(h->C, h->n, h->ldw, h->p, h->d_dscratch, h->mask0, h->one.hubs, s);
+  CK(cudaGetLastError());
+  const Task t1 = make_task(h, popbuf(h, h->one, 1));
+  RET(run_eval(h, t1, true, s));
+  h->ga_task = ga_task_of(h, seed);
+  launch_ga_init(h->ga_task, h->mask0, h->one.fit, s);
+  CK(cudaGetLastError());
+  h->ga_ready = true;
+  h->ga_evals = 1;
+  return USAPHMP_OK;
+}
+
+int usaphmp_ga_run(usaphmp_t h, int32_t generations, void* stream) {
+  if (!h) return fail(USAPHMP_EINVAL, "NULL handle");
+  if (!h->ga_ready) return fail(USAPHMP_EINVAL, "usaphmp_ga_begin first");
+  if (generations < 0) return fail(USAPHMP_EINVAL, "generations < 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int B = h->prm.islands * h->prm.island_size;
+  if (h->prm.use_graph) {
+    if (!h->gexec) {
+      if (!h->graph_stream) CK(cudaStreamCreateWithFlags(&h->graph_stream, cudaStreamNonBlocking));
+      CK(cudaStreamBeginCapture(h->graph_stream, cudaStreamCaptureModeThreadLocal));
+      const int r = enqueue_generation(h, h->graph_stream);
+      cudaGraph_t g = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(h->graph_stream, &g);
+      if (r != USAPHMP_OK) { if (g) cudaGraphDestroy(g); return r; }
+      CK(e);
+      h->graph = g;
+      CK(cudaGraphInstantiate(&h->gexec, h->graph, 0));
+    }
+    for (int i = 0; i < generations; ++i) CK(cudaGraphLaunch(h->gexec, s));
+  } else {
+    for (int i = 0; i < generations; ++i) RET(enqueue_generation(h, s));
+  }
+  h->ga_evals += (int64_t)generations * B;
+  return USAPHMP_OK;
+}
+
+int usaphmp_ga_result(usaphmp_t h, usaphmp_result* best, void* stream) {
+  if (!h || !best) return fail(USAPHMP_EINVAL, "NULL argument");
+  if (!h->ga_ready) return fail(USAPHMP_EINVAL, "usaphmp_ga_begin first");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<uint32_t> m(h->nw);
+  float bf = 0.f;
+  CK(cudaMemcpyAsync(m.data(), h->best, sizeof(uint32_t) * h->nw, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&bf, h->best_fit, sizeof(float), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  RET(check_status(h, s, "usaphmp_ga"));
+  std::vector<int32_t> hubs = mask_to_hubs(m, h->n);
+  if ((int)hubs.size() != h->p) return fail(USAPHMP_ECUDA, "internal: best mask does not hold p hubs");
+  CK(cudaMemcpyAsync(h->one.hubs, hubs.data(), sizeof(int32_t) * h->p, cudaMemcpyHostToDevice, s));
+  const Task t1 = make_task(h, popbuf(h, h->one, 1));
+  TaskSet ts{nullptr, &t1, 1};
+  launch_alloc(ts, true, false, s);
+  CK(cudaGetLastError());
+  launch_rescore(inst_of(h), 1, h->one.hubs, h->one.slot, h->d_rpart, h->d_cost, s);
+  CK(cudaGetLastError());
+  std::vector<uint8_t> sl(h->ns);
+  double cost = 0;
+  CK(cudaMemcpyAsync(sl.data(), h->one.slot, h->ns, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&cost, h->d_cost, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (best->hubs) std::memcpy(best->hubs, hubs.data(), sizeof(int32_t) * h->p);
+  if (best->S)
+    for (int i = 0; i < h->n; ++i) best->S[i] = hubs[sl[i]];
+  best->cost_fp64 = cost;
+  best->cost_fp32 = bf;
+  best->evals = h->ga_evals;
+  return USAPHMP_OK;
+}
+
+int usaphmp_solve(usaphmp_t h, int32_t generations, uint64_t seed, usaphmp_result* best) {
+  if (!h || !best) return fail(USAPHMP_EINVAL, "NULL argument");
+  if (generations < 0) return fail(USAPHMP_EINVAL, "generations < 0");
+  const auto t0 = std::chrono::steady_clock::now();
+  RET(usaphmp_ga_begin(h, seed, h->stream));
+  RET(usaphmp_ga_run(h, generations, h->stream));
+  RET(usaphmp_ga_result(h, best, h->stream));
+  best->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return USAPHMP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,124 @@
+// Shared device-side definitions of the USApHMP library (sm_103a).
+//
+// Layouts (row-major throughout):
+//   W, C          fp32  [n][ldw]   ldw = n rounded up to 8, zero padding
+//   CT            fp32  [n][ldw]   C transposed (aliases C when C is symmetric)
+//   Whi, Wlo      bf16  [n][ldw]   W = Whi + Wlo + O(2^-17 |W|)
+//   O, D          fp32  [n]        originating / destined flow (§3)
+//   mask          u32   [B][nw]    hub mask H of §4.1, bit i%32 of word i/32
+//   hubs          i32   [B][p]     open hubs in ascending node order
+//   slot          u8    [B][ns]    rank in `hubs` of the hub serving node i;
+//                                  ns = n rounded up to 64, padding = 0xFF
+//   chubT         fp32  [B][p][p]  chubT[b][l][k] = C[hubs_b[k], hubs_b[l]]
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace usaphmp {
+
+constexpr int kMaxN = 16384;
+constexpr int kMaxP = 255;
+constexpr uint8_t kSlotPad = 0xFF;
+
+// Bits of the device status word (errors raised inside kernels).
+enum : uint32_t {
+  kStatusBadChromosome = 1u,
+  kStatusTimeout = 2u,
+  kStatusBadValue = 4u,
+};
+
+__host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// Immutable per-instance device data.
+struct DevInst {
+  int n, p, ldw, ns, nw, symmetric;
+  float chi, alpha, delta;
+  const float* W;
+  const float* C;
+  const float* CT;
+  const float* O;
+  const float* D;
+  const __nv_bfloat16* Whi;
+  const __nv_bfloat16* Wlo;
+};
+
+// A population of B chromosomes and its evaluation buffers.
+struct PopBuf {
+  int B;
+  uint32_t* mask;
+  int32_t* hubs;
+  uint8_t* slot;
+  // Optional caller-supplied inputs of the allocation kernel; when set they
+  // are range-checked and copied into `hubs` / `slot` (out-of-range entries
+  // raise kStatusBadChromosome and are replaced by 0).
+  const int32_t* hubs_in;
+  const uint8_t* slot_in;
+  float* t12;      // access terms chi*O*C + delta*D*C per chromosome
+  float* chubT;
+  float* part;     // partial transfer sums (layout set by the evaluator)
+  int npart;       // number of partial rows
+  int part_width;  // 1 (plain: part[r][b]) or p (split: part[r][b*p+l])
+  float* fit;      // fp32 fitness
+  uint32_t* status;  // device status word (kStatus* bits)
+};
+
+// Island GA state (§5): R islands of P chromosomes.
+struct GaState {
+  int R, P, N1, elitist;
+  unsigned long long seed;
+  int* gen;            // device generation counter
+  uint32_t* anc;       // [R][nw]
+  float* anc_fit;      // [R]
+  uint32_t* best;      // [nw]
+  float* best_fit;     // [1]
+};
+
+struct Task {
+  DevInst in;
+  PopBuf pop;
+  GaState ga;
+  const void* tmap_hi;  // CUtensorMap in device memory (split path)
+  const void* tmap_lo;
+};
+
+// Finds the task owning global block `blk` given per-task block offsets
+// (off[0] = 0, off[t+1] = off[t] + blocks of task t).
+__device__ inline int find_task(const int* off, int ntasks, int blk) {
+  int t = 0;
+  while (t + 1 < ntasks && off[t + 1] <= blk) ++t;
+  return t;
+}
+
+__device__ inline float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum in a fixed order (warp butterflies, then warps in order).
+// `red` holds at least blockDim.x/32 floats. Result valid in every thread.
+__device__ inline float block_sum(float v, float* red) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[w] = v;
+  __syncthreads();
+  float s = 0.f;
+  for (int i = 0; i < nw; ++i) s += red[i];
+  return s;
+}
+
+__device__ inline double block_sum_f64(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < nw; ++i) s += red[i];
+  return s;
+}
+
+}  // namespace usaphmp

@@ -1,0 +1,185 @@
+// Plain FP32 CUDA-core evaluator of the transfer term of objective (1), §3:
+//   T3_b = sum_i sum_j W[i][j] * C[h_b(i), h_b(j)]
+//        = sum_i sum_j W[i][j] * Chub_b[s_b(i)][s_b(j)],
+// with Chub_b[k][l] = C[hubs_b[k], hubs_b[l]] (p x p, in shared memory) and
+// s_b the slot codes.  A block takes KB chromosomes and a range of rows; each
+// thread owns 4 consecutive columns, keeps their slot codes (as table
+// offsets) in registers and streams the rows of W once for all KB
+// chromosomes: per (pair, chromosome) one shared-memory gather and one FMA.
+// Partial sums go to part[row_split][b]; the reduction kernel adds them in a
+// fixed order.  Rows are summed in chunks of 32 before joining the running
+// sum, which keeps the fp32 error near (32 + n/32) ulp instead of n ulp.
+#include "common.cuh"
+#include "kernels.cuh"
+
+#include <algorithm>
+
+namespace usaphmp {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__host__ __device__ inline int plain_tpr(int ldw) {
+  // threads per row: enough to cover ldw/4 float4 columns, power of two
+  int need = ldw / 4, t = 32;
+  while (t < need && t < kThreads) t <<= 1;
+  return t;
+}
+
+inline int plain_kb(int p, int ns) {
+  // chromosomes per block: as many as the shared memory comfortably holds
+  for (int kb : {8, 4, 2, 1}) {
+    const size_t bytes = (size_t)kb * p * p * 4 + (size_t)kb * ns;
+    if (bytes <= 96 * 1024) return kb;
+  }
+  return 1;
+}
+
+inline size_t plain_smem(int kb, int p, int ns) {
+  return (size_t)round_up(kb * p * p * 4, 16) + (size_t)kb * ns;
+}
+
+}  // namespace
+
+template <int KB>
+__global__ void __launch_bounds__(kThreads, 2) k_eval_plain(const __grid_constant__ TaskParam tp) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ float red[kThreads / 32];
+  const int t = task_of(tp.bo, blockIdx.x);
+  const Task& T = task_at(tp, t);
+  const int n = T.in.n, p = T.in.p, ldw = T.in.ldw, ns = T.in.ns, B = T.pop.B;
+  const int nrs = T.pop.npart;
+  const int local = blockIdx.x - tp.bo.o[t];
+  const int group = local / nrs, rs = local - group * nrs;
+  const int b0 = group * KB;
+  const int nb = min(KB, B - b0);
+  const int pp = p * p;
+  float* tab = reinterpret_cast<float*>(sm);
+  uint8_t* sl = sm + round_up(KB * pp * 4, 16);
+  const float* __restrict__ C = T.in.C;
+  const float* __restrict__ W = T.in.W;
+  const int32_t* __restrict__ hubs = T.pop.hubs;
+
+  for (int e = threadIdx.x; e < KB * pp; e += kThreads) {
+    const int bb = e / pp, r = e - bb * pp, k = r / p, l = r - k * p;
+    float v = 0.f;
+    if (bb < nb) {
+      const int32_t* hb = hubs + (long long)(b0 + bb) * p;
+      v = C[(long long)hb[k] * ldw + hb[l]];
+    }
+    tab[e] = v;
+  }
+  {
+    const int vec = ns / 16;  // ns is a multiple of 64
+    const uint4* src = reinterpret_cast<const uint4*>(T.pop.slot + (long long)b0 * ns);
+    uint4* dst = reinterpret_cast<uint4*>(sl);
+    for (int e = threadIdx.x; e < KB * vec; e += kThreads) {
+      const int bb = e / vec;
+      dst[e] = (bb < nb) ? src[e] : make_uint4(0u, 0u, 0u, 0u);
+    }
+  }
+  __syncthreads();
+
+  const int chunk = (n + nrs - 1) / nrs;
+  const int r0 = rs * chunk, r1 = min(n, r0 + chunk);
+  const int tpr = plain_tpr(ldw);
+  const int G = kThreads / tpr;
+  const int grp = threadIdx.x / tpr, c4 = threadIdx.x - grp * tpr;
+  const int cols4 = ldw / 4;
+
+  float acc[KB];
+#pragma unroll
+  for (int bb = 0; bb < KB; ++bb) acc[bb] = 0.f;
+
+  for (int cb = c4; cb < cols4; cb += tpr) {
+    const int j0 = cb * 4;
+    int coff[KB][4];
+#pragma unroll
+    for (int bb = 0; bb < KB; ++bb)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int j = j0 + c;
+        coff[bb][c] = bb * pp + ((j < n) ? (int)sl[bb * ns + j] : 0);
+      }
+    for (int i = r0 + grp; i < r1; i += 32 * G) {
+      float part[KB];
+#pragma unroll
+      for (int bb = 0; bb < KB; ++bb) part[bb] = 0.f;
+      const int iend = min(r1, i + 32 * G);
+      for (int ii = i; ii < iend; ii += G) {
+        const float4 w = __ldg(reinterpret_cast<const float4*>(W + (long long)ii * ldw + j0));
+#pragma unroll
+        for (int bb = 0; bb < KB; ++bb) {
+          const float* row = tab + (int)sl[bb * ns + ii] * p;
+          float s = part[bb];
+          s = fmaf(w.x, row[coff[bb][0]], s);
+          s = fmaf(w.y, row[coff[bb][1]], s);
+          s = fmaf(w.z, row[coff[bb][2]], s);
+          s = fmaf(w.w, row[coff[bb][3]], s);
+          part[bb] = s;
+        }
+      }
+#pragma unroll
+      for (int bb = 0; bb < KB; ++bb) acc[bb] += part[bb];
+    }
+  }
+
+#pragma unroll
+  for (int bb = 0; bb < KB; ++bb) {
+    const float s = block_sum(acc[bb], red);
+    if (threadIdx.x == 0 && bb < nb) T.pop.part[(long long)rs * B + b0 + bb] = s;
+  }
+}
+
+int plain_rows(int n, int B) {
+  // Split rows across blocks only when the chromosome groups alone would not
+  // fill the GPU (small populations of large instances).
+  const int groups = (B + 7) / 8;
+  int rs = 1;
+  while (groups * rs < 2 * 152 && rs * 64 < n) rs <<= 1;
+  return rs;
+}
+
+void launch_eval_plain(const TaskSet& ts, cudaStream_t s) {
+  // Tasks of one launch share the block shape; KB is chosen for the largest.
+  int kb = 8;
+  size_t smem = 0;
+  for (int t = 0; t < ts.count; ++t) kb = std::min(kb, plain_kb(ts.h[t].in.p, ts.h[t].in.ns));
+  TaskParam tp = make_param(ts);
+  for (int t = 0; t < ts.count; ++t) {
+    const Task& T = ts.h[t];
+    const int groups = (T.pop.B + kb - 1) / kb;
+    tp.bo.o[t + 1] = tp.bo.o[t] + groups * T.pop.npart;
+    smem = std::max(smem, plain_smem(kb, T.in.p, T.in.ns));
+  }
+  const int blocks = tp.bo.o[ts.count];
+  if (blocks == 0) return;
+  switch (kb) {
+#define USAPHMP_PLAIN_CASE(K)                                 \
+  case K:                                                     \
+    k_eval_plain<K><<<blocks, kThreads, smem, s>>>(tp);       \
+    break;
+    USAPHMP_PLAIN_CASE(8)
+    USAPHMP_PLAIN_CASE(4)
+    USAPHMP_PLAIN_CASE(2)
+    USAPHMP_PLAIN_CASE(1)
+#undef USAPHMP_PLAIN_CASE
+  }
+}
+
+template <class K>
+static void raise_smem_limit(K kernel, int max_smem) {
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - (int)fa.sharedSizeBytes);
+}
+
+void prepare_eval_plain(int max_smem) {
+  raise_smem_limit(k_eval_plain<8>, max_smem);
+  raise_smem_limit(k_eval_plain<4>, max_smem);
+  raise_smem_limit(k_eval_plain<2>, max_smem);
+  raise_smem_limit(k_eval_plain<1>, max_smem);
+}
+
+}  // namespace usaphmp

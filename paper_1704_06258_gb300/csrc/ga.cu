@@ -1,0 +1,326 @@
+// Device GA step of the island model of §5 on n-bit hub masks.
+//
+// Offspring of island r, generation g (one block of two warps per pair of
+// members 2m, 2m+1; warp w builds member q = 2m + w):
+//   1. parent_q = the island's ancestor after one hub <-> spoke exchange
+//      (the move that duplicates the ancestor into a population, §4.1);
+//   2. single-point crossover of the pair (§4.2): one cut c in [1, n-1]
+//      drawn for the pair; child_q keeps bits [0, c) of parent_q and takes
+//      [c, n) from its partner;
+//   3. mutation: one more hub <-> spoke exchange (§4.2);
+//   4. correction back to exactly p hubs (§4.2): close the k-th open node or
+//      open the k-th closed node, k drawn uniformly, until p are open.
+// "k-th" counts in ascending node order.  Every draw comes from a
+// Philox4x32-10 stream keyed by the seed and addressed by (g, q, operator);
+// a value below m is the high word of (32-bit draw) * m.
+//
+// Selection (§5): each island's ancestor becomes its best child (lowest
+// member index on ties, or kept when the elitist flag is set and the child
+// is not strictly better); the best-ever solution changes only on a strict
+// improvement (islands in ascending order); every N1 generations all
+// ancestors are replaced by the best island's ancestor (lowest island on
+// ties), and the generation counter advances.
+#include "common.cuh"
+#include "kernels.cuh"
+
+#include <algorithm>
+
+namespace usaphmp {
+
+namespace {
+
+enum : uint32_t { kOpExchange = 0, kOpCrossover = 1, kOpCorrection = 2, kOpMutation = 3 };
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) { k.x += 0x9E3779B9u; k.y += 0xBB67AE85u; }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+struct Draws {
+  uint4 ctr;
+  uint2 key;
+  uint4 buf;
+  int used;
+  __device__ Draws(unsigned long long seed, uint32_t g, uint32_t q, uint32_t op)
+      : ctr(make_uint4(g, q, op, 0u)), key(make_uint2((uint32_t)seed, (uint32_t)(seed >> 32))), used(4) {}
+  __device__ uint32_t word() {
+    if (used == 4) { buf = philox4x32_10(ctr, key); ctr.w += 1u; used = 0; }
+    const uint32_t w = used == 0 ? buf.x : used == 1 ? buf.y : used == 2 ? buf.z : buf.w;
+    ++used;
+    return w;
+  }
+  __device__ uint32_t below(uint32_t m) { return __umulhi(word(), m); }
+};
+
+__device__ __forceinline__ uint32_t closed_word(uint32_t w, int x, int nw, int n) {
+  w = ~w;
+  if (x == nw - 1 && (n & 31)) w &= (1u << (n & 31)) - 1u;
+  return w;
+}
+
+__device__ int popcount_mask(const uint32_t* mw, int nw) {
+  int c = 0;
+  for (int x = threadIdx.x & 31; x < nw; x += 32) c += __popc(mw[x]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  return c;
+}
+
+// Node id of the k-th open (closed = false) or closed node; warp-uniform.
+__device__ int kth_node(const uint32_t* mw, int nw, int n, uint32_t k, bool closed) {
+  const int lane = threadIdx.x & 31;
+  uint32_t base = 0;
+  for (int c0 = 0; c0 < nw; c0 += 32) {
+    const int x = c0 + lane;
+    uint32_t w = 0;
+    if (x < nw) w = closed ? closed_word(mw[x], x, nw, n) : mw[x];
+    const uint32_t cnt = __popc(w);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    if (k < base + total) {
+      const uint32_t ball = __ballot_sync(0xffffffffu, base + incl > k);
+      const int L = __ffs(ball) - 1;
+      uint32_t ww = __shfl_sync(0xffffffffu, w, L);
+      const uint32_t before = __shfl_sync(0xffffffffu, incl - cnt, L);
+      for (uint32_t kk = k - base - before; kk; --kk) ww &= ww - 1u;
+      return (c0 + L) * 32 + (__ffs(ww) - 1);
+    }
+    base += total;
+  }
+  return -1;
+}
+
+__device__ void flip(uint32_t* mw, int node) {
+  if ((threadIdx.x & 31) == 0 && node >= 0) mw[node >> 5] ^= 1u << (node & 31);
+  __syncwarp();
+}
+
+// One hub <-> spoke exchange; two draws are taken whatever the mask.
+__device__ void exchange(uint32_t* mw, int nw, int n, Draws& d) {
+  const int h = popcount_mask(mw, nw);
+  const uint32_t i = d.below((uint32_t)h);
+  const uint32_t j = d.below((uint32_t)(n - h));
+  if (h > 0 && h < n) {
+    const int a = kth_node(mw, nw, n, i, false);
+    const int b = kth_node(mw, nw, n, j, true);
+    flip(mw, a);
+    flip(mw, b);
+  }
+}
+
+__device__ void correct(uint32_t* mw, int nw, int n, int p, Draws& d) {
+  int h = popcount_mask(mw, nw);
+  while (h > p) {
+    flip(mw, kth_node(mw, nw, n, d.below((uint32_t)h), false));
+    --h;
+  }
+  while (h < p) {
+    flip(mw, kth_node(mw, nw, n, d.below((uint32_t)(n - h)), true));
+    ++h;
+  }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(64) k_children(const __grid_constant__ TaskParam tp) {
+  extern __shared__ uint32_t msm[];
+  const int t = task_of(tp.bo, blockIdx.x);
+  const Task& T = task_at(tp, t);
+  const int n = T.in.n, p = T.in.p, nw = T.in.nw;
+  const int P = T.ga.P;
+  const unsigned long long seed = T.ga.seed;
+  const uint32_t g = (uint32_t)*T.ga.gen;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q0 = 2 * (blockIdx.x - tp.bo.o[t]);
+  const int q = q0 + w;
+  const int r = q / P;
+  uint32_t* par = msm + w * nw;
+  uint32_t* oth = msm + (1 - w) * nw;
+  uint32_t* ch = msm + (2 + w) * nw;
+
+  for (int x = lane; x < nw; x += 32) {
+    uint32_t v = T.ga.anc[(long long)r * nw + x];
+    if (x == nw - 1 && (n & 31)) v &= (1u << (n & 31)) - 1u;  // nodes >= n are never hubs
+    par[x] = v;
+  }
+  __syncwarp();
+  {
+    Draws d(seed, g, (uint32_t)q, kOpExchange);
+    exchange(par, nw, n, d);
+  }
+  __syncthreads();
+  {
+    Draws d(seed, g, (uint32_t)q0, kOpCrossover);
+    const int c = 1 + (int)d.below((uint32_t)(n - 1));
+    for (int x = lane; x < nw; x += 32) {
+      const uint32_t own = par[x], other = oth[x];
+      const int lo = x * 32;
+      uint32_t v;
+      if (lo + 32 <= c) v = own;
+      else if (lo >= c) v = other;
+      else {
+        const uint32_t m = (1u << (c - lo)) - 1u;
+        v = (own & m) | (other & ~m);
+      }
+      ch[x] = v;
+    }
+    __syncwarp();
+  }
+  {
+    Draws d(seed, g, (uint32_t)q, kOpMutation);
+    exchange(ch, nw, n, d);
+  }
+  {
+    Draws d(seed, g, (uint32_t)q, kOpCorrection);
+    correct(ch, nw, n, p, d);
+  }
+  uint32_t* out = T.pop.mask + (long long)q * nw;
+  int32_t* hubs = T.pop.hubs + (long long)q * p;
+  int base = 0;
+  for (int c0 = 0; c0 < nw; c0 += 32) {
+    const int x = c0 + lane;
+    uint32_t v = (x < nw) ? ch[x] : 0u;
+    if (x < nw) out[x] = v;
+    const int cnt = __popc(v);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    int pos = base + incl - cnt;
+    while (v) {
+      hubs[pos++] = x * 32 + (__ffs(v) - 1);
+      v &= v - 1u;
+    }
+    base += __shfl_sync(0xffffffffu, incl, 31);
+  }
+}
+
+// Per island: best child -> ancestor.
+__global__ void k_select_islands(const __grid_constant__ TaskParam tp) {
+  const int t = task_of(tp.bo, blockIdx.x);
+  const Task& T = task_at(tp, t);
+  const int r = blockIdx.x - tp.bo.o[t];
+  const int P = T.ga.P, nw = T.in.nw, lane = threadIdx.x;
+  const float* f = T.pop.fit + (long long)r * P;
+  float v = INFINITY;
+  int idx = 0x7fffffff;
+  for (int j = lane; j < P; j += 32) {
+    const float x = f[j];
+    if (x < v || (x == v && j < idx)) { v = x; idx = j; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ov < v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+  }
+  if (T.ga.elitist && !(v < T.ga.anc_fit[r])) return;
+  const uint32_t* src = T.pop.mask + (long long)(r * P + idx) * nw;
+  uint32_t* dst = T.ga.anc + (long long)r * nw;
+  for (int x = lane; x < nw; x += 32) dst[x] = src[x];
+  if (lane == 0) T.ga.anc_fit[r] = v;
+}
+
+// Per task: best-ever update, merge every N1 generations, generation += 1.
+__global__ void k_select_global(const __grid_constant__ TaskParam tp) {
+  __shared__ float sv[32];
+  __shared__ int si[32];
+  __shared__ int s_rb;
+  const Task& T = task_at(tp, blockIdx.x);
+  const int R = T.ga.R, nw = T.in.nw;
+  float v = INFINITY;
+  int idx = 0x7fffffff;
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    const float x = T.ga.anc_fit[r];
+    if (x < v || (x == v && r < idx)) { v = x; idx = r; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ov < v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+  }
+  if ((threadIdx.x & 31) == 0) { sv[threadIdx.x >> 5] = v; si[threadIdx.x >> 5] = idx; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      if (sv[w] < v || (sv[w] == v && si[w] < idx)) { v = sv[w]; idx = si[w]; }
+    s_rb = idx;
+  }
+  __syncthreads();
+  const int rb = s_rb;
+  const float fb = T.ga.anc_fit[rb];
+  const uint32_t* src = T.ga.anc + (long long)rb * nw;
+  const bool improve = fb < *T.ga.best_fit;
+  __syncthreads();
+  if (improve) {
+    for (int x = threadIdx.x; x < nw; x += blockDim.x) T.ga.best[x] = src[x];
+    if (threadIdx.x == 0) *T.ga.best_fit = fb;
+  }
+  const int g = *T.ga.gen;
+  if ((g + 1) % T.ga.N1 == 0) {
+    for (long long e = threadIdx.x; e < (long long)R * nw; e += blockDim.x) {
+      const int r = (int)(e / nw);
+      if (r != rb) T.ga.anc[e] = src[e - (long long)r * nw];
+    }
+    for (int r = threadIdx.x; r < R; r += blockDim.x)
+      if (r != rb) T.ga.anc_fit[r] = fb;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *T.ga.gen = g + 1;
+}
+
+// Start state: every ancestor and the best-ever = the initial solution.
+__global__ void k_ga_init(const __grid_constant__ Task T, const uint32_t* __restrict__ mask0,
+                          const float* __restrict__ fit0) {
+  const int R = T.ga.R, nw = T.in.nw;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)R * nw;
+       e += (long long)gridDim.x * blockDim.x)
+    T.ga.anc[e] = mask0[e % nw];
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x)
+    T.ga.anc_fit[r] = *fit0;
+  if (blockIdx.x == 0) {
+    for (int x = threadIdx.x; x < nw; x += blockDim.x) T.ga.best[x] = mask0[x];
+    if (threadIdx.x == 0) { *T.ga.best_fit = *fit0; *T.ga.gen = 0; }
+  }
+}
+
+void launch_children(const TaskSet& ts, cudaStream_t s) {
+  TaskParam tp = make_param(ts);
+  int nw = 1;
+  for (int t = 0; t < ts.count; ++t) {
+    tp.bo.o[t + 1] = tp.bo.o[t] + ts.h[t].pop.B / 2;
+    nw = std::max(nw, ts.h[t].in.nw);
+  }
+  const int blocks = tp.bo.o[ts.count];
+  if (blocks == 0) return;
+  k_children<<<blocks, 64, 4 * nw * sizeof(uint32_t), s>>>(tp);
+}
+
+void launch_select(const TaskSet& ts, cudaStream_t s) {
+  TaskParam tp = make_param(ts);
+  for (int t = 0; t < ts.count; ++t) tp.bo.o[t + 1] = tp.bo.o[t] + ts.h[t].ga.R;
+  const int blocks = tp.bo.o[ts.count];
+  if (blocks == 0) return;
+  k_select_islands<<<blocks, 32, 0, s>>>(tp);
+  k_select_global<<<ts.count, 256, 0, s>>>(tp);
+}
+
+void launch_ga_init(const Task& task, const uint32_t* mask0, const float* fit0, cudaStream_t s) {
+  k_ga_init<<<8, 256, 0, s>>>(task, mask0, fit0);
+}
+
+}  // namespace usaphmp

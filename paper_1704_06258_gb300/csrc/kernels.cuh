@@ -1,0 +1,97 @@
+// Host-side launchers of the library's kernels (all stream-ordered, no sync).
+#pragma once
+#include "common.cuh"
+
+namespace usaphmp {
+
+constexpr int kMaxTasks = 64;
+
+// Block ranges of the tasks of one launch: task t owns global blocks
+// [o[t], o[t+1]).  Passed by value so that a captured graph keeps it.
+struct BlockOffsets {
+  int ntasks;
+  int o[kMaxTasks + 1];
+};
+
+__device__ inline int task_of(const BlockOffsets& bo, int blk) {
+  int t = 0;
+  while (t + 1 < bo.ntasks && bo.o[t + 1] <= blk) ++t;
+  return t;
+}
+
+// The tasks of one launch as the host sees them: `h` (host array, read by
+// launchers for sizes) and, for several tasks, the same array in device
+// memory `d`.  A single task with d == nullptr travels by value in the
+// kernel parameters, so nothing has to stay alive in device memory for it.
+struct TaskSet {
+  const Task* d;
+  const Task* h;
+  int count;
+};
+
+// What kernels receive (as a __grid_constant__ parameter).
+struct TaskParam {
+  Task one;
+  const Task* many;
+  BlockOffsets bo;
+};
+
+__device__ __forceinline__ const Task& task_at(const TaskParam& tp, int t) {
+  return tp.many ? tp.many[t] : tp.one;
+}
+
+inline TaskParam make_param(const TaskSet& ts) {
+  TaskParam tp;
+  tp.one = ts.h[0];
+  tp.many = (ts.count == 1 && ts.d == nullptr) ? nullptr : ts.d;
+  tp.bo.ntasks = ts.count;
+  tp.bo.o[0] = 0;
+  return tp;
+}
+
+// setup.cu
+void launch_check_values(const float* W, const float* C, int n, int ldw, uint32_t* status, cudaStream_t s);
+void launch_split_bf16(const float* W, __nv_bfloat16* Whi, __nv_bfloat16* Wlo, long long total, cudaStream_t s);
+void launch_flows(const float* W, int n, int ldw, float* O, float* D, cudaStream_t s);
+void launch_asymmetry(const float* C, int n, int ldw, uint32_t* flag, cudaStream_t s);
+void launch_transpose(const float* C, float* CT, int n, int ldw, cudaStream_t s);
+void launch_middle_nodes(const float* C, int n, int ldw, int p, double* dscratch, uint32_t* mask,
+                         int32_t* hubs, cudaStream_t s);
+
+// canon.cu: validates (hubs, S) in node ids and writes ascending hubs + slots.
+void launch_canon(const int32_t* hubs_in, const int32_t* S, int B, int n, int p, int ns,
+                  int32_t* hubs_out, uint8_t* slot, uint32_t* status, int* bad_index, cudaStream_t s);
+
+// alloc.cu: nearest allocation (or the given slots), access terms t12 and
+// (with_chub) the hub-to-hub cost table chubT.
+void launch_alloc(const TaskSet& ts, bool nearest, bool with_chub, cudaStream_t s);
+
+// eval_plain.cu: fp32 CUDA-core transfer sums into pop.part[r][b]; the
+// number of partial rows per task is plain_rows(n, B).
+int plain_rows(int n, int B);
+void launch_eval_plain(const TaskSet& ts, cudaStream_t s);
+// Raises the dynamic shared-memory limit of the plain kernels (once, outside
+// any stream capture).
+void prepare_eval_plain(int max_smem);
+
+// eval_tc.cu: split-bf16 tcgen05 transfer sums into pop.part[mt][b*p+l]
+// with mt the 128-row tile (ceil(n/128) partial rows).
+void launch_eval_tc(const TaskSet& ts, int num_sms, uint32_t* status, cudaStream_t s);
+int tc_tile_rows();
+void prepare_eval_tc();
+
+// reduce.cu: fit[b] = t12[b] + alpha * (sum of partials, fixed order).
+void launch_reduce(const TaskSet& ts, cudaStream_t s);
+
+// ga.cu: offspring (exchange, crossover, mutation, correction) and selection.
+void launch_children(const TaskSet& ts, cudaStream_t s);
+void launch_select(const TaskSet& ts, cudaStream_t s);
+// Start state of a single-task GA: ancestors and best-ever = mask0, fit0.
+void launch_ga_init(const Task& task, const uint32_t* mask0, const float* fit0, cudaStream_t s);
+
+// rescore.cu: fp64 pair-form objective of B chromosomes of one instance.
+void launch_rescore(const DevInst& in, int B, const int32_t* hubs, const uint8_t* slot,
+                    double* part, double* cost, cudaStream_t s);
+int rescore_parts(int n);
+
+}  // namespace usaphmp

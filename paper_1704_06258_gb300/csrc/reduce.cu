@@ -1,0 +1,36 @@
+// Fitness assembly: fit_b = t12_b + alpha * T3_b, with T3_b the sum of the
+// evaluator's partial transfer sums taken in a fixed order (partial rows
+// ascending, then the p columns of chromosome b ascending), so a
+// chromosome's fitness does not depend on the launch it was evaluated in.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace usaphmp {
+
+__global__ void k_reduce(const __grid_constant__ TaskParam tp) {
+  const int t = task_of(tp.bo, blockIdx.x);
+  const Task& T = task_at(tp, t);
+  const int b = (blockIdx.x - tp.bo.o[t]) * blockDim.x + threadIdx.x;
+  const int B = T.pop.B;
+  if (b >= B) return;
+  const int width = T.pop.part_width;
+  const long long rowlen = (long long)B * width;
+  const float* __restrict__ part = T.pop.part + (long long)b * width;
+  float s = 0.f;
+  for (int r = 0; r < T.pop.npart; ++r) {
+    float rsum = 0.f;
+    for (int l = 0; l < width; ++l) rsum += part[r * rowlen + l];
+    s += rsum;
+  }
+  T.pop.fit[b] = T.pop.t12[b] + T.in.alpha * s;
+}
+
+void launch_reduce(const TaskSet& ts, cudaStream_t s) {
+  TaskParam tp = make_param(ts);
+  for (int t = 0; t < ts.count; ++t) tp.bo.o[t + 1] = tp.bo.o[t] + (ts.h[t].pop.B + 127) / 128;
+  const int blocks = tp.bo.o[ts.count];
+  if (blocks == 0) return;
+  k_reduce<<<blocks, 128, 0, s>>>(tp);
+}
+
+}  // namespace usaphmp

@@ -1,0 +1,165 @@
+"""GPU evaluation vs the FP64 oracle (objective 1 of §3), through the C ABI."""
+import zlib
+
+import numpy as np
+import pytest
+
+from gpu_util import dev, host, need_gpu, stream, torch
+from oracle import cost
+from paper_1704_06258_gb300 import synth
+from paper_1704_06258_gb300.binding import PATH_PLAIN_FP32, PATH_SPLIT_BF16, Instance, UsaphmpError
+
+pytestmark = pytest.mark.gpu
+
+# Relative error bounds against the FP64 oracle: fp32 CUDA-core path and
+# split-bf16 tensor-core path (W = hi + lo, fp32 accumulation).
+TOL = {PATH_PLAIN_FP32: 1e-5, PATH_SPLIT_BF16: 1e-4}
+PATHS = [PATH_PLAIN_FP32, PATH_SPLIT_BF16]
+
+
+def asym_instance(seed, n, p):
+    rng = np.random.default_rng(seed)
+    W = rng.uniform(0, 5, (n, n)).astype(np.float32)
+    C = rng.uniform(1, 50, (n, n)).astype(np.float32)
+    np.fill_diagonal(C, 0)
+    return synth.Instance(f"asym{n}", n, p, W, C)
+
+
+CASES = {
+    "tiny_n10_p3": lambda: synth.tiny(),
+    "n2_p1": lambda: synth.tiny(seed=5, n=2, p=1),
+    "n10_p10": lambda: synth.tiny(seed=6, n=10, p=10),
+    "n200_p5": lambda: synth.urand200(p=5),
+    "n200_p10": lambda: synth.urand200(p=10),
+    "n200_p20": lambda: synth.urand200(p=20),
+    "n333_p7_ragged": lambda: synth.urand200(seed=77, n=333, p=7),
+    "n257_p1": lambda: synth.urand200(seed=78, n=257, p=1),
+    "n129_p64": lambda: synth.urand200(seed=79, n=129, p=64),
+    "asym_n150_p6": lambda: asym_instance(80, 150, 6),
+}
+
+
+def oracle_costs(inst, S):
+    return np.array([cost.pair_cost(inst.W, inst.C, inst.chi, inst.alpha, inst.delta, s) for s in S])
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    need_gpu()
+
+
+@pytest.mark.parametrize("path", PATHS, ids=["plain", "split"])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_eval_matches_oracle(case, path):
+    inst = CASES[case]()
+    B = 37
+    hubs, S = synth.random_population(zlib.crc32(case.encode()) % 1000, inst.n, inst.p, B)
+    ref = oracle_costs(inst, S)
+    with Instance.from_instance(inst) as gi:
+        gi.set_params(path=path)
+        got = gi.eval(hubs, S)
+    rel = np.abs(got - ref) / ref
+    assert rel.max() <= TOL[path], (case, rel.max())
+
+
+@pytest.mark.parametrize("path", PATHS, ids=["plain", "split"])
+def test_eval_dev_equals_eval_and_is_repeatable(path):
+    inst = synth.urand200(p=10)
+    hubs, S = synth.random_population(3, inst.n, inst.p, 300)
+    with Instance.from_instance(inst) as gi:
+        gi.set_params(path=path)
+        a = gi.eval(hubs, S)
+        dh, dS = dev(hubs), dev(S)
+        f = torch.empty(300, dtype=torch.float32, device="cuda")
+        gi.eval_dev(300, dh.data_ptr(), dS.data_ptr(), f.data_ptr(), stream())
+        b = host(f)
+        gi.eval_dev(300, dh.data_ptr(), dS.data_ptr(), f.data_ptr(), stream())
+        c = host(f)
+    np.testing.assert_array_equal(a.astype(np.float32), b)
+    np.testing.assert_array_equal(b, c)
+
+
+@pytest.mark.parametrize("path", PATHS, ids=["plain", "split"])
+def test_fitness_of_a_chromosome_does_not_depend_on_its_batch(path):
+    inst = synth.urand200(seed=9, n=300, p=12)
+    hubs, S = synth.random_population(4, inst.n, inst.p, 200)
+    with Instance.from_instance(inst) as gi:
+        gi.set_params(path=path)
+        whole = gi.eval(hubs, S)
+        alone = np.array([gi.eval(hubs[b:b + 1], S[b:b + 1])[0] for b in (0, 1, 57, 199)])
+        part = gi.eval(hubs[50:120], S[50:120])
+    np.testing.assert_array_equal(whole[[0, 1, 57, 199]], alone)
+    np.testing.assert_array_equal(whole[50:120], part)
+
+
+def test_empty_population():
+    inst = synth.tiny()
+    with Instance.from_instance(inst) as gi:
+        out = gi.eval(np.zeros((0, inst.p), np.int32), np.zeros((0, inst.n), np.int32))
+    assert out.shape == (0,)
+
+
+@pytest.mark.parametrize("path", PATHS, ids=["plain", "split"])
+@pytest.mark.parametrize("mutate,bad", [
+    ("dup_hub", 2), ("spoke_to_nonhub", 5), ("hub_not_self", 1), ("hub_out_of_range", 7), ("S_out_of_range", 3),
+])
+def test_invalid_chromosomes_are_rejected(mutate, bad, path):
+    inst = synth.urand200(seed=11, n=40, p=4)
+    hubs, S = synth.random_population(12, inst.n, inst.p, 10)
+    h = hubs[bad]
+    if mutate == "dup_hub":
+        hubs[bad, 1] = hubs[bad, 0]
+    elif mutate == "spoke_to_nonhub":
+        spoke = next(i for i in range(inst.n) if i not in set(h.tolist()))
+        S[bad, spoke] = spoke
+    elif mutate == "hub_not_self":
+        S[bad, h[0]] = h[1]
+    elif mutate == "hub_out_of_range":
+        hubs[bad, 2] = inst.n
+    elif mutate == "S_out_of_range":
+        S[bad, 0] = -1
+    with Instance.from_instance(inst) as gi:
+        gi.set_params(path=path)
+        with pytest.raises(UsaphmpError) as e:
+            gi.eval(hubs, S)
+        assert e.value.name == "EINVAL_CHROM" and f"chromosome {bad}" in str(e.value)
+        # the handle stays usable
+        good_h, good_S = synth.random_population(13, inst.n, inst.p, 3)
+        assert np.isfinite(gi.eval(good_h, good_S)).all()
+
+
+@pytest.mark.parametrize("what", ["nan_C", "neg_W", "inf_W", "p_gt_n", "p0", "n1"])
+def test_create_rejects_bad_instances(what):
+    inst = synth.tiny()
+    W, C, p, n = inst.W.copy(), inst.C.copy(), inst.p, inst.n
+    if what == "nan_C":
+        C[2, 3] = np.nan
+    elif what == "neg_W":
+        W[1, 4] = -1
+    elif what == "inf_W":
+        W[0, 9] = np.inf
+    elif what == "p_gt_n":
+        p = n + 1
+    elif what == "p0":
+        p = 0
+    elif what == "n1":
+        W, C, p = W[:1, :1], C[:1, :1], 1
+    with pytest.raises(UsaphmpError) as e:
+        Instance(W, C, p)
+    assert e.value.name == "EINVAL"
+
+
+def test_rescore_fp64_matches_oracle():
+    inst = synth.urand200(seed=21, n=300, p=9)
+    hubs, S = synth.random_population(22, inst.n, inst.p, 6)
+    ref = oracle_costs(inst, S)
+    with Instance.from_instance(inst) as gi:
+        hs = np.sort(hubs, axis=1).astype(np.int32)
+        slot = np.full((6, gi.ns), 255, np.uint8)
+        for b in range(6):
+            slot[b, :inst.n] = cost.slots_of(hs[b], S[b])
+        c = torch.empty(6, dtype=torch.float64, device="cuda")
+        d_hs, d_slot = dev(hs), dev(slot)   # keep the tensors alive while the kernels run
+        gi.rescore_fp64_dev(6, d_hs.data_ptr(), d_slot.data_ptr(), c.data_ptr(), stream())
+        got = host(c)
+    np.testing.assert_allclose(got, ref, rtol=1e-12)
