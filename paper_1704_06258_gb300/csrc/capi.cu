@@ -138,11 +138,11 @@ DevInst inst_of(const usaphmp_s* h) {
 bool use_tc(const usaphmp_s* h) { return h->prm.path == USAPHMP_PATH_SPLIT_BF16; }
 
 int part_rows(const usaphmp_s* h, int B) {
-  return use_tc(h) ? (h->n + tc_tile_rows() - 1) / tc_tile_rows() : plain_rows(h->n, B);
+  return use_tc(h) ? tc_part_rows(h->n) : plain_rows(h->n, B);
 }
 
 size_t part_elems(const usaphmp_s* h, int B) {
-  const size_t tc = (size_t)((h->n + tc_tile_rows() - 1) / tc_tile_rows()) * B * h->p;
+  const size_t tc = (size_t)tc_part_rows(h->n) * B * h->p;
   const size_t plain = (size_t)plain_rows(h->n, B) * B;
   return std::max(tc, plain);
 }
@@ -442,7 +442,9 @@ int usaphmp_set_params(usaphmp_t h, const usaphmp_params* prm) {
   if (!h || !prm) return fail(USAPHMP_EINVAL, "NULL argument");
   if (prm->islands < 1 || prm->island_size < 2 || (prm->island_size & 1))
     return fail(USAPHMP_EINVAL, "islands must be >= 1 and island_size even and >= 2");
-  if ((long long)prm->islands * prm->island_size > (1 << 24)) return fail(USAPHMP_EINVAL, "population too large");
+  if ((long long)prm->islands * prm->island_size > (1 << 24) ||
+      (long long)prm->islands * prm->island_size * h->p >= (1ll << 31))
+    return fail(USAPHMP_EINVAL, "population too large");
   if (prm->n1 < 1) return fail(USAPHMP_EINVAL, "n1 must be >= 1");
   if (prm->path != USAPHMP_PATH_PLAIN_FP32 && prm->path != USAPHMP_PATH_SPLIT_BF16)
     return fail(USAPHMP_EINVAL, "unknown path");

@@ -74,10 +74,10 @@ void launch_eval_plain(const TaskSet& ts, cudaStream_t s);
 // any stream capture).
 void prepare_eval_plain(int max_smem);
 
-// eval_tc.cu: split-bf16 tcgen05 transfer sums into pop.part[mt][b*p+l]
-// with mt the 128-row tile (ceil(n/128) partial rows).
+// eval_tc.cu: split-bf16 tcgen05 transfer sums into pop.part[r][b*p+l]
+// with r the 32-row group of W (tc_part_rows(n) = 4*ceil(n/128) rows).
 void launch_eval_tc(const TaskSet& ts, int num_sms, uint32_t* status, cudaStream_t s);
-int tc_tile_rows();
+int tc_part_rows(int n);
 void prepare_eval_tc();
 
 // reduce.cu: fit[b] = t12[b] + alpha * (sum of partials, fixed order).
