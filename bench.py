@@ -1,0 +1,298 @@
+"""Benchmark: fitness evaluations per second of the device GA step on GB300.
+
+One step = one full generation of the island GA on the clustered n=1000,
+p=20 workload (population 4096 = 64 islands x 64): offspring (exchange,
+crossover, mutation, correction), nearest allocation + access terms, the
+transfer term on the split-bf16 tcgen05 evaluator, the fixed-order fitness
+reduction and the selection.  The same generation on the plain fp32
+CUDA-core evaluator is reported beside it.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun): every rank runs its own population of the same size
+(weak scaling, no data-path collective); the step time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fitness evals/s at n=1000,p=20 (split-BF16 TC vs FP32 plain); p50/p99 solve ms"
+UNIT = "evals/s"
+WORKLOAD = "clustered n=1000 p=20, population 4096 (64 islands x 64), one GA generation per step"
+N, P_HUBS, ISLANDS, ISLAND = 1000, 20, 64, 64
+L2_FLUSH_BYTES = 512 << 20
+REF_MEMBERS = 16
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- CPU oracle
+def oracle_island_steps(inst, steps, seed=1, members=ISLAND):
+    """The oracle's own GA generation on one island (offspring, nearest
+    allocation, FP64 pair-form fitness, selection), `steps` times."""
+    from oracle import cost, ga
+    anc = np.zeros((1, inst.n), dtype=bool)
+    anc[0, cost.middle_nodes(inst.C, inst.p)] = True
+    st = ga.State(anc, [np.inf], anc[0], np.inf)
+    evals = 0
+    t0 = time.perf_counter()
+    for g in range(steps):
+        children = ga.make_children(st.ancestors, seed, g, inst.p, members)
+        _, h, _ = ga.allocate_all(inst.C, children)
+        fit = np.array([cost.pair_cost(inst.W, inst.C, inst.chi, inst.alpha, inst.delta, x) for x in h])
+        ga.select(st, children, fit, g, members, 10)
+        evals += len(children)
+    return evals, time.perf_counter() - t0
+
+
+def cpu_baseline(inst, target_s=15.0):
+    evals, dt = oracle_island_steps(inst, 1)
+    steps = max(1, int(target_s / max(dt, 1e-3)))
+    evals, dt = oracle_island_steps(inst, steps)
+    return {"value": evals / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} oracle GA generations of one 64-member island (n=1000, p=20), "
+                      f"FP64 NumPy, single thread, {dt:.1f} s"}
+
+
+# --------------------------------------------------------------- our GPU path
+def timed_generations(gi, steps, warmup, flush, stream, world):
+    import torch
+    gi.ga_begin(1234, stream)
+    for _ in range(warmup):
+        flush.zero_()
+        gi.ga_run_profiled(1, stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    acc = {}
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        flush.zero_()          # L2 flush, outside the per-step events
+        st = gi.ga_run_profiled(1, stream)
+        for k, v in st.items():
+            acc[k] = acc.get(k, 0.0) + v
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    barrier(world)
+    res = gi.ga_result(stream)
+    return {k: v / steps for k, v in acc.items()}, wall, res
+
+
+def e2e_eval(gi, inst, steps, warmup):
+    """usaphmp_eval through the C ABI with pinned host buffers (H2D + D2H per step)."""
+    import torch
+    from paper_1704_06258_gb300 import synth
+    B = ISLANDS * ISLAND
+    hubs, S = synth.random_population(77, inst.n, inst.p, B)
+    hp = torch.from_numpy(hubs).pin_memory().numpy()
+    Sp = torch.from_numpy(S).pin_memory().numpy()
+    for _ in range(max(1, warmup)):
+        gi.eval(hp, Sp)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        f = gi.eval(hp, Sp)
+    dt = time.perf_counter() - t0
+    assert np.isfinite(f).all()
+    return {"value": B * steps / dt, "unit": UNIT, "h2d_bytes_per_step": int(hubs.nbytes + S.nbytes),
+            "d2h_bytes_per_step": int(B * 8), "call": "usaphmp_eval (host hubs + S -> host fitness)"}
+
+
+def run_ours(args):
+    import torch
+    from paper_1704_06258_gb300 import synth
+    from paper_1704_06258_gb300.binding import PATH_PLAIN_FP32, PATH_SPLIT_BF16, Instance
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream().cuda_stream
+    inst = synth.clustered(seed=1003 + rank)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    B = ISLANDS * ISLAND
+    out = {}
+    with Instance.from_instance(inst) as gi:
+        gi.set_params(islands=ISLANDS, island_size=ISLAND, n1=10, path=PATH_PLAIN_FP32)
+        plain, plain_wall, _ = timed_generations(gi, max(3, args.steps // 2), args.warmup, flush, stream, world)
+        gi.set_params(islands=ISLANDS, island_size=ISLAND, n1=10, path=PATH_SPLIT_BF16)
+        with ClockSampler(local) as clk:
+            split, wall, res = timed_generations(gi, args.steps, args.warmup, flush, stream, world)
+        e2e = e2e_eval(gi, inst, steps=max(3, args.steps // 4), warmup=1)
+    ms = max_over_ranks(split["generation"], world)
+    value = B * world / (ms * 1e-3)
+    plain_ms = max_over_ranks(plain["generation"], world)
+    peaks = load_peaks()
+    flops_per_launch = 4.0 * N * N * P_HUBS * B      # 2 GEMMs (hi, lo) x 2 n^2 p per evaluation
+    k1_ms = split["transfer"]
+    achieved = flops_per_launch / (k1_ms * 1e-3) / 1e12
+    if peaks and peaks.get("bf16_tflops_sustained"):
+        peak, peak_src = peaks["bf16_tflops_sustained"], "measured bf16 sustained (MEASURED_PEAKS.json)"
+    else:
+        peak, peak_src = 1700.0, "fallback sustained bf16"
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "path": "split-bf16 tcgen05 (W = bf16 hi + lo, fp32 accumulate)",
+                   "instance": "8 Gaussian clusters sigma 50 in [0,1e4]^2, W lognormal(0,1.5), W_ii=0, "
+                               "C Euclidean, chi=3 alpha=0.75 delta=2, seed 1003+rank",
+                   "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MB write, outside the step events)",
+                   "parallelism": f"weak: one population per GPU x {world}"},
+        "roofline": {"kernel": "k_eval_tc (transfer term)", "bound": "tensor", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
+                     "flops_per_launch": flops_per_launch, "avg_launch_ms": k1_ms},
+        "cpu_baseline": cpu_baseline(inst) if (world == 1 and not args.no_cpu) else None,
+        "e2e": e2e,
+        "gpu_launches": 6 * args.steps,
+        "clocks": clk.summary(),
+        "stage_ms": {k: round(v, 5) for k, v in split.items()},
+        "plain_fp32": {"value": B * world / (plain_ms * 1e-3), "ms_per_step": plain_ms,
+                       "stage_ms": {k: round(v, 5) for k, v in plain.items()}},
+        "split_vs_plain": plain_ms / ms,
+        "best_cost_fp64": res["cost_fp64"], "best_cost_fp32": float(res["cost_fp32"]),
+        "wall_s": wall,
+    }
+    print(json.dumps(line))
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    from paper_1704_06258_gb300 import synth
+    inst = synth.clustered(seed=1003)
+    oracle_island_steps(inst, max(0, args.warmup), members=REF_MEMBERS)
+    evals, dt = oracle_island_steps(inst, args.steps, members=REF_MEMBERS)
+    value = evals / dt
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD + f" (reference step: one {REF_MEMBERS}-member island generation)",
+                   "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} oracle GA generations of one {REF_MEMBERS}-member island, "
+                                   "FP64 NumPy, single thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -64,7 +64,10 @@ _SIGS = {
     "usaphmp_ga_begin": (c_i32, [c_vp, c_u64, c_vp]),
     "usaphmp_ga_run": (c_i32, [c_vp, c_i32, c_vp]),
     "usaphmp_ga_result": (c_i32, [c_vp, ctypes.POINTER(Result), c_vp]),
+    "usaphmp_ga_run_profiled": (c_i32, [c_vp, c_i32, c_vp, ctypes.POINTER(c_f64)]),
 }
+
+STAGES = ("offspring", "allocation", "transfer", "reduce", "select", "generation")
 
 _lib = None
 
@@ -198,6 +201,12 @@ class Instance:
 
     def ga_run(self, generations, stream=0):
         check(lib().usaphmp_ga_run(self.h, generations, stream))
+
+    def ga_run_profiled(self, generations, stream=0):
+        """Runs generations eagerly; returns {stage: summed device ms}."""
+        acc = (c_f64 * 6)()
+        check(lib().usaphmp_ga_run_profiled(self.h, generations, stream, acc))
+        return dict(zip(STAGES, list(acc)))
 
     def ga_result(self, stream=0):
         hubs = np.empty(self.p, dtype=np.int32)

@@ -121,6 +121,7 @@ struct usaphmp_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   cudaStream_t graph_stream = nullptr;
+  cudaEvent_t prof_ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -426,6 +427,8 @@ void usaphmp_destroy(usaphmp_t h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   drop_graph(h);
   if (h->graph_stream) cudaStreamDestroy(h->graph_stream);
+  for (int k = 0; k < 6; ++k)
+    if (h->prof_ev[k]) cudaEventDestroy(h->prof_ev[k]);
   dfree(h->W); dfree(h->C); dfree(h->CTbuf); dfree(h->O); dfree(h->D); dfree(h->Whi); dfree(h->Wlo);
   if (h->tmaps) cudaFree(h->tmaps);
   dfree(h->d_status); dfree(h->d_bad); dfree(h->d_dscratch); dfree(h->d_cost); dfree(h->d_rpart);
@@ -636,6 +639,45 @@ int usaphmp_ga_run(usaphmp_t h, int32_t generations, void* stream) {
     for (int i = 0; i < generations; ++i) RET(enqueue_generation(h, s));
   }
   h->ga_evals += (int64_t)generations * B;
+  return USAPHMP_OK;
+}
+
+int usaphmp_ga_run_profiled(usaphmp_t h, int32_t generations, void* stream, double* stage_ms) {
+  if (!h || !stage_ms) return fail(USAPHMP_EINVAL, "NULL argument");
+  if (!h->ga_ready) return fail(USAPHMP_EINVAL, "usaphmp_ga_begin first");
+  if (generations < 0) return fail(USAPHMP_EINVAL, "generations < 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int k = 0; k < 6; ++k)
+    if (!h->prof_ev[k]) CK(cudaEventCreate(&h->prof_ev[k]));
+  const int B = h->prm.islands * h->prm.island_size;
+  TaskSet ts{nullptr, &h->ga_task, 1};
+  for (int g = 0; g < generations; ++g) {
+    CK(cudaEventRecord(h->prof_ev[0], s));
+    launch_children(ts, s);
+    CK(cudaEventRecord(h->prof_ev[1], s));
+    launch_alloc(ts, true, use_tc(h), s);
+    CK(cudaEventRecord(h->prof_ev[2], s));
+    if (use_tc(h))
+      launch_eval_tc(ts, h->num_sms, h->d_status, s);
+    else
+      launch_eval_plain(ts, s);
+    CK(cudaEventRecord(h->prof_ev[3], s));
+    launch_reduce(ts, s);
+    CK(cudaEventRecord(h->prof_ev[4], s));
+    launch_select(ts, s);
+    CK(cudaEventRecord(h->prof_ev[5], s));
+    CK(cudaGetLastError());
+    CK(cudaEventSynchronize(h->prof_ev[5]));
+    for (int k = 0; k < 5; ++k) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, h->prof_ev[k], h->prof_ev[k + 1]));
+      stage_ms[k] += ms;
+    }
+    float all = 0.f;
+    CK(cudaEventElapsedTime(&all, h->prof_ev[0], h->prof_ev[5]));
+    stage_ms[5] += all;
+    h->ga_evals += B;
+  }
   return USAPHMP_OK;
 }
 

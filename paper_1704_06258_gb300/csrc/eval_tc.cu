@@ -37,7 +37,10 @@ constexpr uint32_t A_BYTES = BM * BK * 2;                 // 16 KB
 constexpr uint32_t B_BYTES = BN * BK * 2;                 // 32 KB
 constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + B_BYTES;   // 64 KB
 constexpr uint32_t TMEM_COLS = 2 * BN;
-constexpr uint32_t kBarOffset = STAGES * STAGE_BYTES;
+constexpr int kTblChrom = 96;                              // chromosomes per tile kept in the epilogue table
+constexpr uint32_t kTblOffset = STAGES * STAGE_BYTES;      // u8 [4 warps][kTblChrom][32 rows]
+constexpr uint32_t kTblBytes = 4 * kTblChrom * 32;
+constexpr uint32_t kBarOffset = kTblOffset + kTblBytes;
 constexpr int kNumBars = 3 * STAGES + 5;
 constexpr size_t kSmemBytes = 1024 + kBarOffset + 8 * kNumBars + 16;
 constexpr uint64_t kTimeoutNs = 2000000000ull;
@@ -237,6 +240,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp >= 4 && warp < 8) {
     // --------------------------------------------------------------- epilogue
     const int quarter = warp & 3;
+    uint8_t* tbl = sm + kTblOffset + quarter * (kTblChrom * 32);
     int tl = 0;
     for (int g = blockIdx.x; g < total_tiles; g += gridDim.x, ++tl) {
       const TileRef tr = decode_tile(tp, g);
@@ -246,16 +250,63 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint8_t* __restrict__ slot = T.pop.slot;
       const float* __restrict__ chubT = T.pop.chubT;
       float* __restrict__ out = T.pop.part + (long long)(tr.m * 4 + quarter) * Bp;
+      const int row = tr.m * BM + quarter * 32 + lane;
+      const bool rvalid = row < n;
+      const int col0 = tr.nb * BN;
+      const int b_first = col0 / p;
+      const int b_last = (min(col0 + BN, Bp) - 1) / p;
+      const int nch = b_last - b_first + 1;
+      const bool use_tbl = nch <= kTblChrom;
+      // Slot codes of this warp's 32 rows for every chromosome of the tile
+      // (u8 table [chromosome][lane]), gathered while the tile's MMAs run.
+      if (use_tbl) {
+        __syncwarp();
+        for (int c0 = 0; c0 < nch; c0 += 8) {
+          uint8_t sv[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            sv[u] = (rvalid && c0 + u < nch) ? __ldg(slot + (long long)(b_first + c0 + u) * ns + row) : (uint8_t)0;
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (c0 + u < nch) tbl[(c0 + u) * 32 + lane] = sv[u];
+        }
+        __syncwarp();
+      }
       const int buf = tl & 1;
       const uint32_t use = (uint32_t)(tl >> 1);
       if (!wait_warp(bars.tfull(buf), use & 1u, abort_flag, status)) break;
       ptx::tc_fence_after();
-      const int row = tr.m * BM + quarter * 32 + lane;
-      const bool rvalid = row < n;
       const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN);
-      const int col0 = tr.nb * BN;
-      int b = col0 / p, l = col0 - b * p, cur_b = -1, s_i = 0;
+      int b = b_first, l = col0 - b_first * p;
       for (int c0 = 0; c0 < BN; c0 += 32) {
+        // factors chubT[b][l][s_b(row)] of the 32 columns: every index is
+        // clamped to a valid entry so that all loads issue back to back; the
+        // columns past B*p and the rows past n are zeroed afterwards.
+        float f[32];
+        if (use_tbl) {
+          int bb = b - b_first, ll = l;
+#pragma unroll
+          for (int cc = 0; cc < 32; ++cc) {
+            const int col = min(col0 + c0 + cc, Bp - 1);
+            const int sr = tbl[min(bb, nch - 1) * 32 + lane];
+            f[cc] = __ldg(chubT + (long long)col * p + sr);
+            if (++ll == p) { ll = 0; ++bb; }
+          }
+        } else {
+          int bb = b, ll = l;
+#pragma unroll
+          for (int cc = 0; cc < 32; ++cc) {
+            const int col = min(col0 + c0 + cc, Bp - 1);
+            const int sr = __ldg(slot + (long long)min(bb, b_last) * ns + (rvalid ? row : 0));
+            f[cc] = __ldg(chubT + (long long)col * p + min(sr, p - 1));
+            if (++ll == p) { ll = 0; ++bb; }
+          }
+        }
+#pragma unroll
+        for (int cc = 0; cc < 32; ++cc) {
+          if (++l == p) { l = 0; ++b; }
+          if (!rvalid || col0 + c0 + cc >= Bp) f[cc] = 0.f;
+        }
         float v[32];
         ptx::tmem_ld_32x32(taddr + (uint32_t)c0, v);
         if (c0 + 32 == BN) {
@@ -263,19 +314,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           ptx::mbar_arrive(bars.tempty(buf));
         }
 #pragma unroll
-        for (int cc = 0; cc < 32; ++cc) {
-          const int col = col0 + c0 + cc;
-          float prod = 0.f;
-          if (col < Bp) {
-            if (b != cur_b) {
-              cur_b = b;
-              s_i = rvalid ? (int)slot[(long long)b * ns + row] : 0;
-            }
-            if (rvalid) prod = v[cc] * __ldg(chubT + (long long)col * p + s_i);
-          }
-          v[cc] = prod;
-          if (++l == p) { l = 0; ++b; }
-        }
+        for (int cc = 0; cc < 32; ++cc) v[cc] *= f[cc];
         const float sum = transpose_sum32(v);
         const int col = col0 + c0 + lane;
         if (col < Bp) out[col] = sum;
@@ -298,14 +337,22 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t lrep = (uint32_t)(valid ? col - b * p : 0) * 0x01010101u;
       const uint8_t* srow = T.pop.slot + (long long)b * ns;
       const uint32_t swz = (uint32_t)(r & 7);
+      const uint4* src = reinterpret_cast<const uint4*>(srow);
+      const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+      // slot codes of the next K block are loaded one block ahead
+      uint4 n0 = zero4, n1 = zero4, n2 = zero4, n3 = zero4;
+      if (valid) { n0 = __ldg(src); n1 = __ldg(src + 1); n2 = __ldg(src + 2); n3 = __ldg(src + 3); }
       for (int kb = 0; kb < nk; ++kb, ++it) {
+        const uint4 q0 = n0, q1 = n1, q2 = n2, q3 = n3;
+        if (valid && kb + 1 < nk) {
+          const uint4* nx = src + (kb + 1) * (BK / 16);
+          n0 = __ldg(nx); n1 = __ldg(nx + 1); n2 = __ldg(nx + 2); n3 = __ldg(nx + 3);
+        }
         const int s = it % STAGES;
         const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
         if (!(ok = wait_warp(bars.empty(s), ph ^ 1u, abort_flag, status))) break;
         const uint32_t dst = base + s * STAGE_BYTES + 2 * A_BYTES + (uint32_t)r * 128u;
         if (valid) {
-          const uint4* src = reinterpret_cast<const uint4*>(srow + kb * BK);
-          const uint4 q0 = __ldg(src), q1 = __ldg(src + 1), q2 = __ldg(src + 2), q3 = __ldg(src + 3);
           st_shared_v4(dst + ((0u ^ swz) << 4), onehot8(q0.x, q0.y, lrep));
           st_shared_v4(dst + ((1u ^ swz) << 4), onehot8(q0.z, q0.w, lrep));
           st_shared_v4(dst + ((2u ^ swz) << 4), onehot8(q1.x, q1.y, lrep));
