@@ -3,7 +3,8 @@
 //   slot_b(i) = argmin_l C[i, hubs_b[l]]   (lowest node id on ties; a hub
 //               serves itself),
 //   t12_b     = sum_i chi*O_i*C[i,h(i)] + delta*D_i*C[h(i),i],
-// plus, for the tensor-core evaluator, chubT_b[l][k] = C[hubs_b[k], hubs_b[l]].
+// plus, for the tensor-core evaluator, the hub-to-hub cost table
+// chub_b[k][l] = C[hubs_b[k], hubs_b[l]] (layout in common.cuh).
 // One block per chromosome; C[i, hub] is read as CT[hub][i], so the p loads
 // of each node are coalesced across the block.
 #include "common.cuh"
@@ -66,10 +67,11 @@ __global__ void __launch_bounds__(256) k_alloc(const __grid_constant__ TaskParam
   const float s = block_sum(acc, red);
   if (threadIdx.x == 0) T.pop.t12[b] = s;
   if (with_chub) {
-    float* __restrict__ ch = T.pop.chubT + (long long)b * p * p;
-    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
-      const int l = e / p, k = e - l * p;
-      ch[e] = C[(long long)hs[k] * ldw + hs[l]];
+    const int hst = chub_hstride(p), cst = chub_cstride(p);
+    float* __restrict__ ch = T.pop.chub + (long long)b * cst;
+    for (int e = threadIdx.x; e < cst; e += blockDim.x) {
+      const int k = e / hst, l = e - k * hst;
+      ch[e] = (k < p && l < p) ? C[(long long)hs[k] * ldw + hs[l]] : 0.f;
     }
   }
 }

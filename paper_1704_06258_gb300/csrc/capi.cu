@@ -64,11 +64,11 @@ struct Pop {
   int32_t* hubs = nullptr;
   uint8_t* slot = nullptr;
   float* t12 = nullptr;
-  float* chubT = nullptr;
+  float* chub = nullptr;
   float* part = nullptr;
   float* fit = nullptr;
   void release() {
-    dfree(mask); dfree(hubs); dfree(slot); dfree(t12); dfree(chubT); dfree(part); dfree(fit);
+    dfree(mask); dfree(hubs); dfree(slot); dfree(t12); dfree(chub); dfree(part); dfree(fit);
     cap = 0;
     part_cap = 0;
   }
@@ -143,7 +143,7 @@ int part_rows(const usaphmp_s* h, int B) {
 }
 
 size_t part_elems(const usaphmp_s* h, int B) {
-  const size_t tc = (size_t)tc_part_rows(h->n) * B * h->p;
+  const size_t tc = (size_t)tc_part_rows(h->n) * B;
   const size_t plain = (size_t)plain_rows(h->n, B) * B;
   return std::max(tc, plain);
 }
@@ -156,7 +156,7 @@ int ensure_pop(usaphmp_s* h, Pop& P, int B) {
   CK(dalloc(&P.hubs, (size_t)B * h->p));
   CK(dalloc(&P.slot, (size_t)B * h->ns));
   CK(dalloc(&P.t12, (size_t)B));
-  CK(dalloc(&P.chubT, (size_t)B * h->p * h->p));
+  CK(dalloc(&P.chub, (size_t)B * chub_cstride(h->p)));
   CK(dalloc(&P.part, need_part));
   CK(dalloc(&P.fit, (size_t)B));
   P.cap = B;
@@ -168,9 +168,8 @@ PopBuf popbuf(const usaphmp_s* h, const Pop& P, int B) {
   PopBuf pb;
   pb.B = B;
   pb.mask = P.mask; pb.hubs = P.hubs; pb.slot = P.slot; pb.t12 = P.t12;
-  pb.chubT = P.chubT; pb.part = P.part; pb.fit = P.fit;
+  pb.chub = P.chub; pb.part = P.part; pb.fit = P.fit;
   pb.npart = part_rows(h, B);
-  pb.part_width = use_tc(h) ? h->p : 1;
   pb.hubs_in = nullptr;
   pb.slot_in = nullptr;
   pb.status = h->d_status;
@@ -205,7 +204,7 @@ int reset_status(usaphmp_s* h, cudaStream_t s) {
   return USAPHMP_OK;
 }
 
-// Transfer term + reduction for a task whose hubs/slots/t12/chubT are set.
+// Transfer term + reduction for a task whose hubs/slots/t12/chub are set.
 int run_transfer(usaphmp_s* h, const Task& task, cudaStream_t s) {
   TaskSet ts{nullptr, &task, 1};
   if (use_tc(h))

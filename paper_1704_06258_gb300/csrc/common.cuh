@@ -9,7 +9,11 @@
 //   hubs          i32   [B][p]     open hubs in ascending node order
 //   slot          u8    [B][ns]    rank in `hubs` of the hub serving node i;
 //                                  ns = n rounded up to 64, padding = 0xFF
-//   chubT         fp32  [B][p][p]  chubT[b][l][k] = C[hubs_b[k], hubs_b[l]]
+//   chub          fp32  [B][cstride]  hub-to-hub costs of chromosome b:
+//                 chub[b][k * hstride + l] = C[hubs_b[k], hubs_b[l]], with
+//                 hstride = p rounded up to odd (bank-conflict-free rows) and
+//                 cstride = p * hstride rounded up to a multiple of 4 floats
+//                 (16-byte aligned blocks for bulk copies)
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -29,6 +33,8 @@ enum : uint32_t {
 };
 
 __host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+__host__ __device__ inline int chub_hstride(int p) { return p | 1; }
+__host__ __device__ inline int chub_cstride(int p) { return round_up(p * chub_hstride(p), 4); }
 
 // Immutable per-instance device data.
 struct DevInst {
@@ -55,10 +61,9 @@ struct PopBuf {
   const int32_t* hubs_in;
   const uint8_t* slot_in;
   float* t12;      // access terms chi*O*C + delta*D*C per chromosome
-  float* chubT;
+  float* chub;
   float* part;     // partial transfer sums (layout set by the evaluator)
-  int npart;       // number of partial rows
-  int part_width;  // 1 (plain: part[r][b]) or p (split: part[r][b*p+l])
+  int npart;       // number of partial rows: part[r][b], r < npart
   float* fit;      // fp32 fitness
   uint32_t* status;  // device status word (kStatus* bits)
 };

@@ -4,7 +4,7 @@
 // A_b[j][l] = [s_b(j) == l] (n x p), the transfer term is
 //   T3_b = sum_i sum_l M_b[i][l] * Chub_b[s_b(i)][l],   M_b = W A_b,
 // i.e. the inner sum over j of objective (1) grouped by the hub serving j.
-// All chromosomes of a launch are packed side by side as the columns
+// The chromosomes of a launch are packed side by side as the columns
 // (b, l) -> b*p + l of one GEMM  D = W [A_1 .. A_B]  (n x n times n x B*p):
 //   * W enters as two bf16 operands, W = Whi + Wlo + O(2^-17 |W|), loaded by
 //     TMA with the 128-byte swizzle; both are multiplied by the same one-hot
@@ -12,17 +12,20 @@
 //   * the one-hot operand is never stored in global memory: producer warps
 //     expand it from the u8 slot codes straight into shared memory, in the
 //     same swizzled K-major layout;
-//   * the epilogue reads the accumulator from TMEM, multiplies each element
-//     D[i][(b,l)] by Chub_b[s_b(i)][l] = chubT[b][l][s_b(i)] and sums the 32
-//     rows held by each warp with a fixed butterfly, writing one partial per
-//     (32-row group, column); D itself never leaves the SM.
+//   * a column tile holds whole chromosomes only (CPT = floor(256/p) of them,
+//     MMA width N = CPT*p rounded up to 16), so the epilogue can finish each
+//     chromosome inside the tile: every thread (one row i of W) forms
+//     sum_l D[i][(b,l)] * Chub_b[s_b(i)][l] with the Chub tables of the
+//     tile's chromosomes bulk-copied into shared memory, and a warp
+//     butterfly adds the 32 rows; one partial per (32-row group, chromosome)
+//     is written, D itself never leaves the SM.
 // Persistent kernel, one CTA per SM, warp roles: 0 TMA, 1 MMA (+ TMEM
-// allocation), 4-7 epilogue (TMEM lane quarters 0-3), 8-15 one-hot
-// producers.  Tiles are 128 rows x 256 columns x 64-deep K blocks, three
-// shared-memory stages, two TMEM accumulators (512 columns) so the epilogue of
-// one tile overlaps the MMAs of the next.  Every wait is bounded: after
-// kTimeoutNs the kernel raises kStatusTimeout, drains its own copies and
-// MMAs, frees TMEM and returns.
+// allocation), 4-11 epilogue (warp w reads TMEM lane quarter w%4 and one half
+// of the tile's chromosomes), 12-19 one-hot producers.  Tiles are 128 rows x N columns x 64-deep K blocks, three
+// shared-memory stages, two TMEM accumulators (2 x 256 columns) so the
+// epilogue of one tile overlaps the MMAs of the next.  Every wait is bounded:
+// after kTimeoutNs the kernel raises kStatusTimeout, drains its own copies
+// and MMAs, frees TMEM and returns.
 #include "common.cuh"
 #include "kernels.cuh"
 #include "tc_ptx.cuh"
@@ -31,20 +34,24 @@ namespace usaphmp {
 
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 3;
-constexpr int kThreads = 512;
+constexpr int BM = 128, BNMAX = 256, BK = 64, STAGES = 3;
+constexpr int kThreads = 640;
+constexpr int kEpiWarps = 8;
+constexpr int kProdWarp0 = 4 + kEpiWarps;
 constexpr uint32_t A_BYTES = BM * BK * 2;                 // 16 KB
-constexpr uint32_t B_BYTES = BN * BK * 2;                 // 32 KB
+constexpr uint32_t B_BYTES = BNMAX * BK * 2;              // 32 KB
 constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + B_BYTES;   // 64 KB
-constexpr uint32_t TMEM_COLS = 2 * BN;
-constexpr int kTblChrom = 96;                              // chromosomes per tile kept in the epilogue table
-constexpr uint32_t kTblOffset = STAGES * STAGE_BYTES;      // u8 [4 warps][kTblChrom][32 rows]
+constexpr uint32_t TMEM_COLS = 2 * BNMAX;
+constexpr uint32_t kSlabOffset = STAGES * STAGE_BYTES;    // Chub tables of the tile's chromosomes
+constexpr uint32_t kSlabBytes = 23552;
+constexpr int kTblChrom = 86;                              // slot-code table: u8 [4 warps][86][32 rows]
+constexpr uint32_t kTblOffset = kSlabOffset + kSlabBytes;
 constexpr uint32_t kTblBytes = 4 * kTblChrom * 32;
 constexpr uint32_t kBarOffset = kTblOffset + kTblBytes;
-constexpr int kNumBars = 3 * STAGES + 5;
-constexpr size_t kSmemBytes = 1024 + kBarOffset + 8 * kNumBars + 16;
+constexpr int kNumBars = 3 * STAGES + 7;
+constexpr size_t kSmemBytes = 1024 + kBarOffset + 8 * kNumBars + 8;
 constexpr uint64_t kTimeoutNs = 2000000000ull;
-constexpr uint32_t IDESC = ptx::idesc_bf16_f32(BM, BN);
+static_assert(kSmemBytes <= 232448, "shared memory budget");
 
 struct Bars {
   uint32_t base;
@@ -54,6 +61,8 @@ struct Bars {
   __device__ uint32_t tfull(int b) const { return base + 8 * (3 * STAGES + b); }
   __device__ uint32_t tempty(int b) const { return base + 8 * (3 * STAGES + 2 + b); }
   __device__ uint32_t drain() const { return base + 8 * (3 * STAGES + 4); }
+  __device__ uint32_t slab_full() const { return base + 8 * (3 * STAGES + 5); }
+  __device__ uint32_t slab_empty() const { return base + 8 * (3 * STAGES + 6); }
 };
 
 // Single-thread bounded wait.  Returns false on timeout or when another role
@@ -102,6 +111,21 @@ __device__ bool wait_warp(uint32_t bar, uint32_t parity, volatile int* abort_fla
   }
 }
 
+// Column geometry of a task: whole chromosomes per tile.
+struct Geo {
+  int cpt;    // chromosomes per column tile
+  int nt;     // column tiles
+  bool slab;  // Chub tables of a full tile fit in the shared slab
+};
+
+__host__ __device__ __forceinline__ Geo geo_of(int p, int B) {
+  Geo g;
+  g.cpt = BNMAX / p;
+  g.nt = (B + g.cpt - 1) / g.cpt;
+  g.slab = (size_t)g.cpt * chub_cstride(p) * 4 <= kSlabBytes;
+  return g;
+}
+
 struct TileRef {
   int task, m, nb;
 };
@@ -111,8 +135,7 @@ __device__ __forceinline__ TileRef decode_tile(const TaskParam& tp, int g) {
   r.task = task_of(tp.bo, g);
   const Task& T = task_at(tp, r.task);
   const int local = g - tp.bo.o[r.task];
-  const int Bp = T.pop.B * T.in.p;
-  const int nt = (Bp + BN - 1) / BN;
+  const int nt = geo_of(T.in.p, T.pop.B).nt;
   r.m = local / nt;
   r.nb = local - r.m * nt;
   return r;
@@ -132,22 +155,6 @@ __device__ __forceinline__ uint4 onehot8(uint32_t w0, uint32_t w1, uint32_t lrep
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint4 v) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
                : "memory");
-}
-
-// Lane L ends with the sum over the 32 lanes of v[L] (fixed butterfly order).
-__device__ __forceinline__ float transpose_sum32(float* v) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int step = 16; step >= 1; step >>= 1) {
-    const bool upper = (lane & step) != 0;
-#pragma unroll
-    for (int c = 0; c < step; ++c) {
-      const float send = upper ? v[c] : v[c + step];
-      const float keep = upper ? v[c + step] : v[c];
-      v[c] = keep + __shfl_xor_sync(0xffffffffu, send, step);
-    }
-  }
-  return v[0];
 }
 
 }  // namespace
@@ -171,9 +178,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       ptx::mbar_init(bars.tfull(b), 1);
-      ptx::mbar_init(bars.tempty(b), 128);
+      ptx::mbar_init(bars.tempty(b), 32 * kEpiWarps);
     }
     ptx::mbar_init(bars.drain(), 1);
+    ptx::mbar_init(bars.slab_full(), 1);
+    ptx::mbar_init(bars.slab_empty(), kEpiWarps);
     *abort_flag = 0;
     ptx::fence_mbar_init();
   }
@@ -212,12 +221,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool ok = true;
     for (int g = blockIdx.x; g < total_tiles && ok; g += gridDim.x, ++tl) {
       const TileRef tr = decode_tile(tp, g);
-      const int nk = (task_at(tp, tr.task).in.n + BK - 1) / BK;
+      const Task& T = task_at(tp, tr.task);
+      const int p = T.in.p;
+      const Geo geo = geo_of(p, T.pop.B);
+      const int nchrom = min(geo.cpt, T.pop.B - tr.nb * geo.cpt);
+      const uint32_t idesc = ptx::idesc_bf16_f32(BM, round_up(nchrom * p, 16));
+      const int nk = (T.in.n + BK - 1) / BK;
       const int buf = tl & 1;
       const uint32_t use = (uint32_t)(tl >> 1);
       if (!(ok = wait_one(bars.tempty(buf), (use & 1u) ^ 1u, abort_flag, status))) break;
       ptx::tc_fence_after();
-      const uint32_t d = tmem + (uint32_t)(buf * BN);
+      const uint32_t d = tmem + (uint32_t)(buf * BNMAX);
       for (int kb = 0; kb < nk; ++kb, ++it) {
         const int s = it % STAGES;
         const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
@@ -228,8 +242,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int k = 0; k < BK / 16; ++k) {
           const uint64_t bdesc = ptx::sw128_desc(bt + 32 * k);
-          ptx::mma_bf16(d, ptx::sw128_desc(a_hi + 32 * k), bdesc, IDESC, (kb | k) != 0);
-          ptx::mma_bf16(d, ptx::sw128_desc(a_lo + 32 * k), bdesc, IDESC, 1u);
+          ptx::mma_bf16(d, ptx::sw128_desc(a_hi + 32 * k), bdesc, idesc, (kb | k) != 0);
+          ptx::mma_bf16(d, ptx::sw128_desc(a_lo + 32 * k), bdesc, idesc, 1u);
         }
         ptx::tc_commit(bars.empty(s));
       }
@@ -237,105 +251,141 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     ptx::tc_commit(bars.drain());
     wait_drain(bars.drain(), 0);
-  } else if (warp >= 4 && warp < 8) {
+  } else if (warp >= 4 && warp < 4 + kEpiWarps) {
     // --------------------------------------------------------------- epilogue
-    const int quarter = warp & 3;
+    const int quarter = warp & 3, half = (warp - 4) >> 2;
     uint8_t* tbl = sm + kTblOffset + quarter * (kTblChrom * 32);
+    const float* slab = reinterpret_cast<const float*>(sm + kSlabOffset);
     int tl = 0;
     for (int g = blockIdx.x; g < total_tiles; g += gridDim.x, ++tl) {
       const TileRef tr = decode_tile(tp, g);
       const Task& T = task_at(tp, tr.task);
-      const int n = T.in.n, p = T.in.p, ns = T.in.ns;
-      const int Bp = T.pop.B * p;
-      const uint8_t* __restrict__ slot = T.pop.slot;
-      const float* __restrict__ chubT = T.pop.chubT;
-      float* __restrict__ out = T.pop.part + (long long)(tr.m * 4 + quarter) * Bp;
+      const int n = T.in.n, p = T.in.p, ns = T.in.ns, B = T.pop.B;
+      const Geo geo = geo_of(p, B);
+      const int b0 = tr.nb * geo.cpt;
+      const int nchrom = min(geo.cpt, B - b0);
+      const int hst = chub_hstride(p), cst = chub_cstride(p);
+      const float* __restrict__ chub = T.pop.chub + (long long)b0 * cst;
+      const uint8_t* __restrict__ slot = T.pop.slot + (long long)b0 * ns;
       const int row = tr.m * BM + quarter * 32 + lane;
       const bool rvalid = row < n;
-      const int col0 = tr.nb * BN;
-      const int b_first = col0 / p;
-      const int b_last = (min(col0 + BN, Bp) - 1) / p;
-      const int nch = b_last - b_first + 1;
-      const bool use_tbl = nch <= kTblChrom;
-      // Slot codes of this warp's 32 rows for every chromosome of the tile
-      // (u8 table [chromosome][lane]), gathered while the tile's MMAs run.
+      const bool use_tbl = nchrom <= kTblChrom;
+      // this warp's chromosomes: [cb, ce)
+      const int split = (nchrom + 1) >> 1;
+      const int cb = half ? split : 0, ce = half ? nchrom : split;
+      // Chub tables of the tile's chromosomes -> slab (single buffer, one
+      // bulk copy issued once every epilogue warp has released the slab).
+      if (warp == 4 && lane == 0) {
+        if (wait_one(bars.slab_empty(), (uint32_t)(tl & 1) ^ 1u, abort_flag, status)) {
+          if (geo.slab) {
+            const uint32_t bytes = (uint32_t)(nchrom * cst * 4);
+            ptx::mbar_arrive_expect_tx(bars.slab_full(), bytes);
+            ptx::bulk_load(base + kSlabOffset, chub, bytes, bars.slab_full());
+          } else {
+            ptx::mbar_arrive(bars.slab_full());
+          }
+        }
+      }
+      // slot codes of this warp's 32 rows for its chromosomes
       if (use_tbl) {
         __syncwarp();
-        for (int c0 = 0; c0 < nch; c0 += 8) {
+        for (int c0 = cb; c0 < ce; c0 += 8) {
           uint8_t sv[8];
 #pragma unroll
           for (int u = 0; u < 8; ++u)
-            sv[u] = (rvalid && c0 + u < nch) ? __ldg(slot + (long long)(b_first + c0 + u) * ns + row) : (uint8_t)0;
+            sv[u] = (rvalid && c0 + u < ce) ? __ldg(slot + (long long)(c0 + u) * ns + row) : (uint8_t)0;
 #pragma unroll
           for (int u = 0; u < 8; ++u)
-            if (c0 + u < nch) tbl[(c0 + u) * 32 + lane] = sv[u];
+            if (c0 + u < ce) tbl[(c0 + u) * 32 + lane] = sv[u];
         }
         __syncwarp();
       }
       const int buf = tl & 1;
       const uint32_t use = (uint32_t)(tl >> 1);
       if (!wait_warp(bars.tfull(buf), use & 1u, abort_flag, status)) break;
+      if (!wait_warp(bars.slab_full(), (uint32_t)(tl & 1), abort_flag, status)) break;
       ptx::tc_fence_after();
-      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN);
-      int b = b_first, l = col0 - b_first * p;
-      for (int c0 = 0; c0 < BN; c0 += 32) {
-        // factors chubT[b][l][s_b(row)] of the 32 columns: every index is
-        // clamped to a valid entry so that all loads issue back to back; the
-        // columns past B*p and the rows past n are zeroed afterwards.
-        float f[32];
-        if (use_tbl) {
-          int bb = b - b_first, ll = l;
+      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BNMAX);
+      float* __restrict__ out = T.pop.part + (long long)(tr.m * 4 + quarter) * B + b0;
+      const float* fbase = geo.slab ? slab : chub;
+      const int col_b = cb * p, col_e = ce * p;   // this warp's columns
+      constexpr int CH = 16;   // TMEM columns per chunk
+      const int k0 = col_b / CH, k1 = (col_e + CH - 1) / CH;
+      // running state at the first column of chunk k0: chromosome c, column l
+      int c = (k0 * CH) / p, l = k0 * CH - c * p;
+      float acc = 0.f;
+      for (int k = k0; k < k1; ++k) {
+        // factors chub_b[s_b(row)][l] of the chunk's columns, gathered
+        // branch-free: chromosome and slot indices are clamped to valid
+        // entries (the values of columns outside [col_b, col_e) are unused)
+        float f[CH];
+        {
+          int c2 = c, l2 = l;
+          if (use_tbl) {
 #pragma unroll
-          for (int cc = 0; cc < 32; ++cc) {
-            const int col = min(col0 + c0 + cc, Bp - 1);
-            const int sr = tbl[min(bb, nch - 1) * 32 + lane];
-            f[cc] = __ldg(chubT + (long long)col * p + sr);
-            if (++ll == p) { ll = 0; ++bb; }
-          }
-        } else {
-          int bb = b, ll = l;
+            for (int cc = 0; cc < CH; ++cc) {
+              const int cl = max(min(c2, ce - 1), 0);
+              const int sr = min((int)tbl[cl * 32 + lane], p - 1);
+              f[cc] = fbase[cl * cst + sr * hst + l2];
+              if (++l2 == p) { l2 = 0; ++c2; }
+            }
+          } else {
 #pragma unroll
-          for (int cc = 0; cc < 32; ++cc) {
-            const int col = min(col0 + c0 + cc, Bp - 1);
-            const int sr = __ldg(slot + (long long)min(bb, b_last) * ns + (rvalid ? row : 0));
-            f[cc] = __ldg(chubT + (long long)col * p + min(sr, p - 1));
-            if (++ll == p) { ll = 0; ++bb; }
+            for (int cc = 0; cc < CH; ++cc) {
+              const int cl = max(min(c2, ce - 1), 0);
+              const int sr = rvalid ? min((int)__ldg(slot + (long long)cl * ns + row), p - 1) : 0;
+              f[cc] = fbase[cl * cst + sr * hst + l2];
+              if (++l2 == p) { l2 = 0; ++c2; }
+            }
           }
         }
-#pragma unroll
-        for (int cc = 0; cc < 32; ++cc) {
-          if (++l == p) { l = 0; ++b; }
-          if (!rvalid || col0 + c0 + cc >= Bp) f[cc] = 0.f;
-        }
-        float v[32];
-        ptx::tmem_ld_32x32(taddr + (uint32_t)c0, v);
-        if (c0 + 32 == BN) {
+        float v[CH];
+        ptx::tmem_ld_32x16(taddr + (uint32_t)(k * CH), v);
+        if (k + 1 == k1) {
           ptx::tc_fence_before();
           ptx::mbar_arrive(bars.tempty(buf));
         }
 #pragma unroll
-        for (int cc = 0; cc < 32; ++cc) v[cc] *= f[cc];
-        const float sum = transpose_sum32(v);
-        const int col = col0 + c0 + lane;
-        if (col < Bp) out[col] = sum;
+        for (int cc = 0; cc < CH; ++cc) {
+          const int col = k * CH + cc;
+          if (col >= col_b && col < col_e) {
+            acc = fmaf(v[cc], rvalid ? f[cc] : 0.f, acc);
+            if (l == p - 1) {
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+              if (lane == 0) out[c] = acc;
+              acc = 0.f;
+            }
+          }
+          if (++l == p) { l = 0; ++c; }
+        }
       }
+      if (k0 >= k1) {   // no chromosome for this warp: still release the accumulator
+        ptx::tc_fence_before();
+        ptx::mbar_arrive(bars.tempty(buf));
+      }
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(bars.slab_empty());
     }
-  } else if (warp >= 8) {
+  } else if (warp >= kProdWarp0) {
     // -------------------------------------------------------- one-hot producers
-    const int r = threadIdx.x - 256;
+    const int r = threadIdx.x - 32 * kProdWarp0;
     int it = 0;
     bool ok = true;
     for (int g = blockIdx.x; g < total_tiles && ok; g += gridDim.x) {
       const TileRef tr = decode_tile(tp, g);
       const Task& T = task_at(tp, tr.task);
-      const int n = T.in.n, p = T.in.p, ns = T.in.ns;
-      const int Bp = T.pop.B * p;
+      const int n = T.in.n, p = T.in.p, ns = T.in.ns, B = T.pop.B;
+      const Geo geo = geo_of(p, B);
+      const int b0 = tr.nb * geo.cpt;
+      const int nchrom = min(geo.cpt, B - b0);
+      const int nmma = round_up(nchrom * p, 16);
       const int nk = (n + BK - 1) / BK;
-      const int col = tr.nb * BN + r;
-      const bool valid = col < Bp;
-      const int b = valid ? col / p : 0;
-      const uint32_t lrep = (uint32_t)(valid ? col - b * p : 0) * 0x01010101u;
-      const uint8_t* srow = T.pop.slot + (long long)b * ns;
+      const bool valid = r < nchrom * p;   // rows in [nchrom*p, nmma) are zero
+      const bool write = r < nmma;
+      const int c = valid ? r / p : 0;
+      const uint32_t lrep = (uint32_t)(valid ? r - c * p : 0) * 0x01010101u;
+      const uint8_t* srow = T.pop.slot + (long long)(b0 + c) * ns;
       const uint32_t swz = (uint32_t)(r & 7);
       const uint4* src = reinterpret_cast<const uint4*>(srow);
       const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
@@ -361,10 +411,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           st_shared_v4(dst + ((5u ^ swz) << 4), onehot8(q2.z, q2.w, lrep));
           st_shared_v4(dst + ((6u ^ swz) << 4), onehot8(q3.x, q3.y, lrep));
           st_shared_v4(dst + ((7u ^ swz) << 4), onehot8(q3.z, q3.w, lrep));
-        } else {
-          const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+        } else if (write) {
 #pragma unroll
-          for (uint32_t c = 0; c < 8; ++c) st_shared_v4(dst + (c << 4), z);
+          for (uint32_t q = 0; q < 8; ++q) st_shared_v4(dst + (q << 4), zero4);
         }
         ptx::fence_proxy_async_smem();
         ptx::mbar_arrive(bars.full_oh(s));
@@ -391,8 +440,7 @@ void launch_eval_tc(const TaskSet& ts, int num_sms, uint32_t* status, cudaStream
   for (int t = 0; t < ts.count; ++t) {
     const Task& T = ts.h[t];
     const int mt = (T.in.n + BM - 1) / BM;
-    const int nt = (T.pop.B * T.in.p + BN - 1) / BN;
-    tp.bo.o[t + 1] = tp.bo.o[t] + mt * nt;
+    tp.bo.o[t + 1] = tp.bo.o[t] + (T.pop.B > 0 ? mt * geo_of(T.in.p, T.pop.B).nt : 0);
   }
   const int total = tp.bo.o[ts.count];
   if (total == 0) return;

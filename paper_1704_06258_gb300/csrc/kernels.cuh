@@ -63,7 +63,7 @@ void launch_canon(const int32_t* hubs_in, const int32_t* S, int B, int n, int p,
                   int32_t* hubs_out, uint8_t* slot, uint32_t* status, int* bad_index, cudaStream_t s);
 
 // alloc.cu: nearest allocation (or the given slots), access terms t12 and
-// (with_chub) the hub-to-hub cost table chubT.
+// (with_chub) the hub-to-hub cost table chub.
 void launch_alloc(const TaskSet& ts, bool nearest, bool with_chub, cudaStream_t s);
 
 // eval_plain.cu: fp32 CUDA-core transfer sums into pop.part[r][b]; the
@@ -74,8 +74,8 @@ void launch_eval_plain(const TaskSet& ts, cudaStream_t s);
 // any stream capture).
 void prepare_eval_plain(int max_smem);
 
-// eval_tc.cu: split-bf16 tcgen05 transfer sums into pop.part[r][b*p+l]
-// with r the 32-row group of W (tc_part_rows(n) = 4*ceil(n/128) rows).
+// eval_tc.cu: split-bf16 tcgen05 transfer sums into pop.part[r][b] with r
+// the 32-row group of W (tc_part_rows(n) = 4*ceil(n/128) rows).
 void launch_eval_tc(const TaskSet& ts, int num_sms, uint32_t* status, cudaStream_t s);
 int tc_part_rows(int n);
 void prepare_eval_tc();

@@ -1,7 +1,7 @@
 // Fitness assembly: fit_b = t12_b + alpha * T3_b, with T3_b the sum of the
-// evaluator's partial transfer sums taken in a fixed order (partial rows
-// ascending, then the p columns of chromosome b ascending), so a
-// chromosome's fitness does not depend on the launch it was evaluated in.
+// evaluator's partial transfer sums part[r][b] taken in a fixed order (r
+// ascending), so a chromosome's fitness does not depend on the launch it was
+// evaluated in.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -13,15 +13,9 @@ __global__ void k_reduce(const __grid_constant__ TaskParam tp) {
   const int b = (blockIdx.x - tp.bo.o[t]) * blockDim.x + threadIdx.x;
   const int B = T.pop.B;
   if (b >= B) return;
-  const int width = T.pop.part_width;
-  const long long rowlen = (long long)B * width;
-  const float* __restrict__ part = T.pop.part + (long long)b * width;
+  const float* __restrict__ part = T.pop.part + b;
   float s = 0.f;
-  for (int r = 0; r < T.pop.npart; ++r) {
-    float rsum = 0.f;
-    for (int l = 0; l < width; ++l) rsum += part[r * rowlen + l];
-    s += rsum;
-  }
+  for (int r = 0; r < T.pop.npart; ++r) s += part[(long long)r * B];
   T.pop.fit[b] = T.pop.t12[b] + T.in.alpha * s;
 }
 
