@@ -19,7 +19,8 @@ used here (and by the library) are:
 * Correction (§4.2): while more than p nodes are open, close the
   below(h)-th open node; while fewer, open the below(n - h)-th closed node.
 * Selection (§5): island r's ancestor becomes its child with the smallest
-  fitness (lowest member index on ties).  The best-ever solution is replaced
+  fitness (lowest member index on ties; a NaN fitness, which has no order,
+  ranks after every number).  The best-ever solution is replaced
   only by a strictly smaller fitness, islands scanned in ascending order.
   Every N1 generations (the outer loop) every island's ancestor becomes the
   ancestor of the island whose ancestor fitness is smallest (lowest island on
@@ -126,10 +127,16 @@ class State:
         self.best_fit = float(best_fit)
 
 
+def _rank(x):
+    """Selection key: NaN ranks after every number."""
+    x = np.asarray(x, dtype=np.float64)
+    return np.where(np.isnan(x), np.inf, x)
+
+
 def select(state, children, fitness, g, P, N1, elitist=False):
     """Inner-loop selection and the outer-loop merge of §5, in place on `state`."""
     R = state.ancestors.shape[0]
-    fitness = np.asarray(fitness)
+    fitness = _rank(fitness)
     for r in range(R):
         f = fitness[r * P:(r + 1) * P]
         j = int(np.argmin(f))           # first minimum: lowest member index
@@ -137,7 +144,7 @@ def select(state, children, fitness, g, P, N1, elitist=False):
             continue
         state.ancestors[r] = children[r * P + j]
         state.anc_fit[r] = f[j]
-    rb = int(np.argmin(state.anc_fit))  # first minimum: lowest island
+    rb = int(np.argmin(_rank(state.anc_fit)))  # first minimum: lowest island
     if state.anc_fit[rb] < state.best_fit:
         state.best = state.ancestors[rb].copy()
         state.best_fit = float(state.anc_fit[rb])

@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           st_shared_v4(dst + ((7u ^ swz) << 4), onehot8(q3.z, q3.w, lrep));
         } else if (write) {
 #pragma unroll
-          for (uint32_t q = 0; q < 8; ++q) st_shared_v4(dst + (q << 4), zero4);
+          for (uint32_t q = 0; q < 8; ++q) st_shared_v4(dst + ((q ^ swz) << 4), zero4);
         }
         ptx::fence_proxy_async_smem();
         ptx::mbar_arrive(bars.full_oh(s));

@@ -208,6 +208,10 @@ __global__ void __launch_bounds__(64) k_children(const __grid_constant__ TaskPar
   }
 }
 
+// Selection key: a NaN fitness ranks after every number (as +inf), so an
+// argmin always lands on a member of the island.
+__device__ __forceinline__ float rank_key(float x) { return isnan(x) ? INFINITY : x; }
+
 // Per island: best child -> ancestor.
 __global__ void k_select_islands(const __grid_constant__ TaskParam tp) {
   const int t = task_of(tp.bo, blockIdx.x);
@@ -218,7 +222,7 @@ __global__ void k_select_islands(const __grid_constant__ TaskParam tp) {
   float v = INFINITY;
   int idx = 0x7fffffff;
   for (int j = lane; j < P; j += 32) {
-    const float x = f[j];
+    const float x = rank_key(f[j]);
     if (x < v || (x == v && j < idx)) { v = x; idx = j; }
   }
 #pragma unroll
@@ -244,7 +248,7 @@ __global__ void k_select_global(const __grid_constant__ TaskParam tp) {
   float v = INFINITY;
   int idx = 0x7fffffff;
   for (int r = threadIdx.x; r < R; r += blockDim.x) {
-    const float x = T.ga.anc_fit[r];
+    const float x = rank_key(T.ga.anc_fit[r]);
     if (x < v || (x == v && r < idx)) { v = x; idx = r; }
   }
 #pragma unroll

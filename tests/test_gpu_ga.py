@@ -90,14 +90,17 @@ def test_children_bit_exact(n, p, R, P, seed, g):
 
 def _select_case(R, P, nw, rng, ties):
     fit = rng.uniform(10, 20, R * P).astype(np.float32)
-    if ties:
+    if ties == "nan":
+        fit[rng.random(R * P) < 0.5] = np.nan
+        fit[:P] = np.nan            # an island with no number at all
+    elif ties:
         fit = np.round(fit).astype(np.float32)
     return fit
 
 
 @pytest.mark.parametrize("R,P,g,N1,ties,elitist", [
     (4, 8, 0, 10, False, 0), (4, 8, 9, 10, True, 0), (7, 6, 19, 5, True, 0), (3, 64, 2, 3, False, 1),
-    (5, 4, 4, 5, True, 1),
+    (5, 4, 4, 5, True, 1), (4, 8, 9, 10, "nan", 0),
 ])
 def test_selection_bit_exact(R, P, g, N1, ties, elitist):
     n, p = 70, 5

@@ -134,6 +134,17 @@ def test_selection_rules():
     assert st2.anc_fit[1] == 1.0
 
 
+def test_selection_ranks_nan_last():
+    n, P = 6, 4
+    children = np.eye(8, n, dtype=bool)
+    st = ga.State(np.zeros((2, n), bool), [10.0, 10.0], np.zeros(n, bool), 10.0)
+    fit = np.array([np.nan, 3.0, np.nan, 5.0, np.nan, np.nan, np.nan, np.nan])
+    ga.select(st, children, fit, g=0, P=P, N1=10)
+    np.testing.assert_array_equal(st.ancestors[0], children[1])   # NaN never preferred
+    np.testing.assert_array_equal(st.ancestors[1], children[4])   # all NaN: first member
+    assert st.anc_fit[1] == np.inf and st.best_fit == 3.0
+
+
 @pytest.mark.slow
 def test_ga_reaches_best_nearest_solution_on_tiny_instance():
     inst = synth.tiny()
