@@ -161,6 +161,34 @@ int usaphmp_ga_result(usaphmp_t h, usaphmp_result* best, void* stream);
  * 4 selection (§5), 5 the whole generation. */
 int usaphmp_ga_run_profiled(usaphmp_t h, int32_t generations, void* stream, double* stage_ms);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free entry point.  The paper has no counterpart: this exists for
+ * callers that cannot call cudaMalloc -- code that must stay inside a device
+ * memory budget or pool owned by a host application, or a latency-critical
+ * loop where cudaMalloc's implicit device synchronisation is not acceptable.
+ *
+ * Same result as usaphmp_rescore_fp64_dev (fp64 pair form of eq. 1) without a
+ * handle: every input and the output are caller device buffers, and the
+ * function neither allocates nor frees anything.  Its per-block partial sums
+ * go to a fixed scratch array compiled into the library: 131072 doubles
+ * (1 MiB), present on every GPU that loads the library until the process
+ * exits.
+ *   W, C   fp32 [n][n] row-major (dense, no padding)
+ *   hubs   i32  [B][p] ascending node ids; slot u8 [B][n] (rank in hubs of the
+ *          hub serving node i); cost fp64 [B] out.
+ * Sizes: 2 <= n <= 16384, 1 <= p <= min(n, 255), and B * min(n, 128) must not
+ * exceed 131072 (else USAPHMP_EINVAL, nothing launched).  Enqueued on
+ * `stream`, no synchronisation.
+ * The first call on a device looks up the scratch array's device address on
+ * the current device; make that first call before any stream capture.  All
+ * calls share the one scratch array (every call rewrites the entries it reads,
+ * nothing needs to start at zero), so calls whose work overlaps on the GPU --
+ * on different streams or from different threads -- race and return wrong
+ * costs: order them on one stream or synchronise between them. */
+int usaphmp_rescore_fp64_noalloc(int32_t n, int32_t p, int32_t B, const float* W, const float* C,
+                                 double chi, double alpha, double delta, const int32_t* hubs,
+                                 const uint8_t* slot, double* cost, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

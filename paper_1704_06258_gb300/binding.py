@@ -65,6 +65,8 @@ _SIGS = {
     "usaphmp_ga_run": (c_i32, [c_vp, c_i32, c_vp]),
     "usaphmp_ga_result": (c_i32, [c_vp, ctypes.POINTER(Result), c_vp]),
     "usaphmp_ga_run_profiled": (c_i32, [c_vp, c_i32, c_vp, ctypes.POINTER(c_f64)]),
+    "usaphmp_rescore_fp64_noalloc": (c_i32, [c_i32, c_i32, c_i32, c_vp, c_vp, c_f64, c_f64, c_f64, c_vp, c_vp,
+                                             c_vp, c_vp]),
 }
 
 STAGES = ("offspring", "allocation", "transfer", "reduce", "select", "generation")
@@ -100,6 +102,12 @@ def check(rc):
 
 def _ptr(a):
     return a.ctypes.data_as(c_vp)
+
+
+def rescore_fp64_noalloc(n, p, B, W_ptr, C_ptr, chi, alpha, delta, hubs_ptr, slot_ptr, cost_ptr, stream=0):
+    """usaphmp_rescore_fp64_noalloc: no handle, no allocation (dense W, C, slot)."""
+    check(lib().usaphmp_rescore_fp64_noalloc(n, p, B, W_ptr, C_ptr, chi, alpha, delta, hubs_ptr, slot_ptr,
+                                             cost_ptr, stream))
 
 
 class Instance:

@@ -407,6 +407,8 @@ std::vector<int32_t> mask_to_hubs(const std::vector<uint32_t>& m, int n) {
 
 }  // namespace
 
+int usaphmp::report_error(int code, const std::string& msg) { return fail(code, msg); }
+
 extern "C" {
 
 const char* usaphmp_last_error(void) { return g_err.c_str(); }

@@ -1,5 +1,7 @@
 // Host-side launchers of the library's kernels (all stream-ordered, no sync).
 #pragma once
+#include <string>
+
 #include "common.cuh"
 
 namespace usaphmp {
@@ -93,5 +95,8 @@ void launch_ga_init(const Task& task, const uint32_t* mask0, const float* fit0, 
 void launch_rescore(const DevInst& in, int B, const int32_t* hubs, const uint8_t* slot,
                     double* part, double* cost, cudaStream_t s);
 int rescore_parts(int n);
+
+// capi.cu: records the calling thread's last error message; returns `code`.
+int report_error(int code, const std::string& msg);
 
 }  // namespace usaphmp
