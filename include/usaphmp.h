@@ -162,6 +162,40 @@ int usaphmp_ga_result(usaphmp_t h, usaphmp_result* best, void* stream);
 int usaphmp_ga_run_profiled(usaphmp_t h, int32_t generations, void* stream, double* stage_ms);
 
 /* ---------------------------------------------------------------------------
+ * Serving: continuous batching of GA solve requests of differing n and p on
+ * one GPU.  Requests queue in FIFO order and are admitted while at most
+ * `max_active` (<= 64) run and the device bytes of the running ones
+ * (usaphmp_server_footprint) stay within `hbm_budget_bytes`; a request that
+ * alone exceeds the budget finishes with USAPHMP_EBUSY.  Each
+ * usaphmp_server_step admits what fits, then runs one generation (§5) of
+ * every running request with one launch per kernel over all of them, then
+ * rescores (fp64) and releases the requests that have run all their
+ * generations.  A request's result does not depend on which other requests
+ * ran beside it.  The server is not thread-safe.
+ * ------------------------------------------------------------------------- */
+typedef struct usaphmp_server_s* usaphmp_server_t;
+
+int usaphmp_server_create(int64_t hbm_budget_bytes, int32_t max_active, int32_t path, usaphmp_server_t* out);
+
+/* Queues a request (W, C host n*n, copied); *ticket identifies it. */
+int usaphmp_server_submit(usaphmp_server_t s, int32_t n, int32_t p, const float* W, const float* C, double chi,
+                          double alpha, double delta, int32_t islands, int32_t island_size, int32_t generations,
+                          uint64_t seed, int64_t* ticket);
+
+/* One tick (see above); reports how many requests run and wait. */
+int usaphmp_server_step(usaphmp_server_t s, int32_t* n_active, int32_t* n_pending);
+
+/* 1: finished, *out filled (hubs/S into caller buffers of p and n entries;
+ * ms = submit-to-finish wall time) and the ticket forgotten; 0: not finished;
+ * < 0: the request failed (message in usaphmp_last_error). */
+int usaphmp_server_poll(usaphmp_server_t s, int64_t ticket, usaphmp_result* out);
+
+/* Device bytes a request of this shape holds while it runs. */
+int usaphmp_server_footprint(int32_t n, int32_t p, int32_t islands, int32_t island_size, int64_t* bytes);
+
+void usaphmp_server_destroy(usaphmp_server_t s);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free entry point.  The paper has no counterpart: this exists for
  * callers that cannot call cudaMalloc -- code that must stay inside a device
  * memory budget or pool owned by a host application, or a latency-critical

@@ -67,6 +67,13 @@ _SIGS = {
     "usaphmp_ga_run_profiled": (c_i32, [c_vp, c_i32, c_vp, ctypes.POINTER(c_f64)]),
     "usaphmp_rescore_fp64_noalloc": (c_i32, [c_i32, c_i32, c_i32, c_vp, c_vp, c_f64, c_f64, c_f64, c_vp, c_vp,
                                              c_vp, c_vp]),
+    "usaphmp_server_create": (c_i32, [c_i64, c_i32, c_i32, ctypes.POINTER(c_vp)]),
+    "usaphmp_server_submit": (c_i32, [c_vp, c_i32, c_i32, c_vp, c_vp, c_f64, c_f64, c_f64, c_i32, c_i32, c_i32,
+                                      c_u64, ctypes.POINTER(c_i64)]),
+    "usaphmp_server_step": (c_i32, [c_vp, ctypes.POINTER(c_i32), ctypes.POINTER(c_i32)]),
+    "usaphmp_server_poll": (c_i32, [c_vp, c_i64, ctypes.POINTER(Result)]),
+    "usaphmp_server_footprint": (c_i32, [c_i32, c_i32, c_i32, c_i32, ctypes.POINTER(c_i64)]),
+    "usaphmp_server_destroy": (None, [c_vp]),
 }
 
 STAGES = ("offspring", "allocation", "transfer", "reduce", "select", "generation")
@@ -222,3 +229,65 @@ class Instance:
         r = Result(hubs.ctypes.data_as(ctypes.POINTER(c_i32)), S.ctypes.data_as(ctypes.POINTER(c_i32)))
         check(lib().usaphmp_ga_result(self.h, ctypes.byref(r), stream))
         return {"hubs": hubs, "S": S, "cost_fp64": r.cost_fp64, "cost_fp32": r.cost_fp32, "evals": r.evals}
+
+
+class Server:
+    """Continuous-batching serving loop (a ``usaphmp_server_t``)."""
+
+    def __init__(self, hbm_budget_bytes, max_active=32, path=PATH_SPLIT_BF16):
+        h = c_vp()
+        check(lib().usaphmp_server_create(int(hbm_budget_bytes), max_active, path, ctypes.byref(h)))
+        self.h = h
+        self._shape = {}
+
+    def submit(self, W, C, p, chi=3.0, alpha=0.75, delta=2.0, islands=8, island_size=64, generations=200,
+               seed=0):
+        W = np.ascontiguousarray(W, dtype=np.float32)
+        C = np.ascontiguousarray(C, dtype=np.float32)
+        t = c_i64()
+        check(lib().usaphmp_server_submit(self.h, W.shape[0], p, _ptr(W), _ptr(C), chi, alpha, delta, islands,
+                                          island_size, generations, seed, ctypes.byref(t)))
+        self._shape[t.value] = (W.shape[0], p)
+        return t.value
+
+    def step(self):
+        a, q = c_i32(), c_i32()
+        check(lib().usaphmp_server_step(self.h, ctypes.byref(a), ctypes.byref(q)))
+        return a.value, q.value
+
+    def poll(self, ticket):
+        """None while running; the result dict once finished (raises on failure)."""
+        n, p = self._shape[ticket]
+        hubs = np.empty(p, dtype=np.int32)
+        S = np.empty(n, dtype=np.int32)
+        r = Result(hubs.ctypes.data_as(ctypes.POINTER(c_i32)), S.ctypes.data_as(ctypes.POINTER(c_i32)))
+        rc = lib().usaphmp_server_poll(self.h, ticket, ctypes.byref(r))
+        if rc == 0:
+            return None
+        del self._shape[ticket]
+        check(0 if rc == 1 else rc)
+        return {"hubs": hubs, "S": S, "cost_fp64": r.cost_fp64, "cost_fp32": r.cost_fp32, "evals": r.evals,
+                "ms": r.ms}
+
+    @staticmethod
+    def footprint(n, p, islands, island_size):
+        b = c_i64()
+        check(lib().usaphmp_server_footprint(n, p, islands, island_size, ctypes.byref(b)))
+        return b.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().usaphmp_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

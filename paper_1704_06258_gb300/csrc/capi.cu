@@ -409,6 +409,23 @@ std::vector<int32_t> mask_to_hubs(const std::vector<uint32_t>& m, int n) {
 
 int usaphmp::report_error(int code, const std::string& msg) { return fail(code, msg); }
 
+const Task& usaphmp::handle_ga_task(const usaphmp_s* h) { return h->ga_task; }
+bool usaphmp::handle_uses_tc(const usaphmp_s* h) { return use_tc(h); }
+void usaphmp::handle_note_generations(usaphmp_s* h, int g) {
+  h->ga_evals += (int64_t)g * h->prm.islands * h->prm.island_size;
+}
+
+size_t usaphmp::handle_device_bytes(int n, int p, int R, int P) {
+  const size_t ldw = round_up(n, 8), ns = round_up(n, 64), nw = (n + 31) / 32;
+  const size_t B = (size_t)R * P;
+  const size_t mat = (size_t)n * ldw;
+  size_t bytes = 3 * mat * 4 + 2 * mat * 2 + 4 * (size_t)n * 4 + 256;   // W, C, CT, Whi, Wlo, O, D, misc
+  const size_t rows = std::max((size_t)tc_part_rows(n), (size_t)plain_rows(n, (int)B));
+  const size_t per_chrom = nw * 4 + (size_t)p * 4 + ns + 8 + (size_t)chub_cstride(p) * 4 + rows * 4;
+  bytes += (B + 1) * per_chrom + (size_t)R * (nw * 4 + 4) + 3 * nw * 4 + 1024;
+  return bytes;
+}
+
 extern "C" {
 
 const char* usaphmp_last_error(void) { return g_err.c_str(); }

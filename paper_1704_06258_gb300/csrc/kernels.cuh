@@ -100,3 +100,15 @@ int rescore_parts(int n);
 int report_error(int code, const std::string& msg);
 
 }  // namespace usaphmp
+
+// capi.cu: what the serving loop needs from a handle (after usaphmp_ga_begin).
+struct usaphmp_s;
+namespace usaphmp {
+const Task& handle_ga_task(const usaphmp_s* h);
+bool handle_uses_tc(const usaphmp_s* h);
+void handle_note_generations(usaphmp_s* h, int generations);
+// Device bytes a handle holds for an instance of n nodes and p hubs running
+// the GA with population B = R * P (upper bound: counts a transposed C).
+size_t handle_device_bytes(int n, int p, int R, int P);
+
+}  // namespace usaphmp

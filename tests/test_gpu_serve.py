@@ -1,0 +1,134 @@
+"""Serving loop: continuous batching, admission, alone-vs-mix determinism."""
+import numpy as np
+import pytest
+
+from gpu_util import need_gpu
+from oracle import cost
+from paper_1704_06258_gb300 import synth
+from paper_1704_06258_gb300.binding import PATH_PLAIN_FP32, PATH_SPLIT_BF16, Instance, Server, UsaphmpError
+
+pytestmark = pytest.mark.gpu
+
+GB = 1 << 30
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def _requests():
+    out = []
+    for r, (n, p, gens) in enumerate([(60, 3, 12), (250, 11, 9), (97, 7, 15), (400, 20, 6), (33, 5, 10)]):
+        inst = synth.clustered(seed=7000 + r, n=n, p=p)
+        out.append((inst, gens, 100 + r))
+    return out
+
+
+def _drain(server, tickets):
+    res = {}
+    for _ in range(10000):
+        server.step()
+        for t in list(tickets):
+            r = server.poll(t)
+            if r is not None:
+                res[t] = r
+                tickets.remove(t)
+        if not tickets:
+            return res
+    raise AssertionError("server did not finish")
+
+
+@pytest.mark.parametrize("path", [PATH_PLAIN_FP32, PATH_SPLIT_BF16], ids=["plain", "split"])
+def test_results_alone_equal_results_in_the_mix(path):
+    reqs = _requests()
+    alone = []
+    for inst, gens, seed in reqs:
+        with Server(4 * GB, max_active=8, path=path) as s:
+            t = s.submit(inst.W, inst.C, inst.p, islands=2, island_size=16, generations=gens, seed=seed)
+            alone.append(_drain(s, [t])[t])
+    with Server(4 * GB, max_active=3, path=path) as s:
+        tickets = []
+        # staggered arrivals: two now, the rest while those run
+        for k, (inst, gens, seed) in enumerate(reqs):
+            tickets.append(s.submit(inst.W, inst.C, inst.p, islands=2, island_size=16, generations=gens, seed=seed))
+            if k >= 1:
+                s.step()
+        mixed = _drain(s, list(tickets))
+    for (inst, gens, seed), a, t in zip(reqs, alone, tickets):
+        m = mixed[t]
+        np.testing.assert_array_equal(a["hubs"], m["hubs"])
+        np.testing.assert_array_equal(a["S"], m["S"])
+        assert a["cost_fp32"] == m["cost_fp32"] and a["cost_fp64"] == m["cost_fp64"]
+        assert m["evals"] == 1 + gens * 32
+        cost.check_allocation(inst.n, m["hubs"], m["S"])
+        ref = cost.pair_cost(inst.W, inst.C, inst.chi, inst.alpha, inst.delta, m["S"])
+        assert m["cost_fp64"] == pytest.approx(ref, rel=1e-12)
+
+
+def test_served_result_equals_direct_solve():
+    inst = synth.clustered(seed=7100, n=180, p=9)
+    with Instance.from_instance(inst) as gi:
+        gi.set_params(islands=2, island_size=16, n1=10, path=PATH_SPLIT_BF16)
+        direct = gi.solve(11, 5)
+    with Server(4 * GB, max_active=4, path=PATH_SPLIT_BF16) as s:
+        t = s.submit(inst.W, inst.C, inst.p, islands=2, island_size=16, generations=11, seed=5)
+        served = _drain(s, [t])[t]
+    np.testing.assert_array_equal(direct["hubs"], served["hubs"])
+    assert direct["cost_fp32"] == served["cost_fp32"]
+
+
+def test_admission_respects_the_memory_budget_and_slots():
+    reqs = _requests()
+    fp = [Server.footprint(i.n, i.p, 2, 16) for i, _, _ in reqs]
+    budget = max(fp) + min(fp)          # never room for the two largest at once
+    with Server(budget, max_active=2, path=PATH_SPLIT_BF16) as s:
+        tickets = [s.submit(i.W, i.C, i.p, islands=2, island_size=16, generations=g, seed=sd) for i, g, sd in reqs]
+        peak = 0
+        done = {}
+        for _ in range(10000):
+            active, pending = s.step()
+            peak = max(peak, active)
+            for t in list(tickets):
+                r = s.poll(t)
+                if r is not None:
+                    done[t] = r
+                    tickets.remove(t)
+            if not tickets:
+                break
+        assert not tickets and peak <= 2
+
+
+def test_oversized_request_is_refused():
+    inst = synth.clustered(seed=7200, n=300, p=5)
+    with Server(1 << 20, max_active=2) as s:
+        t = s.submit(inst.W, inst.C, inst.p, islands=2, island_size=16, generations=3)
+        s.step()
+        with pytest.raises(UsaphmpError) as e:
+            s.poll(t)
+        assert e.value.name == "EBUSY"
+
+
+def test_invalid_request_fails_alone():
+    good = synth.clustered(seed=7300, n=80, p=4)
+    bad_W = good.W.copy()
+    bad_W[3, 4] = -1.0
+    with Server(4 * GB, max_active=4) as s:
+        tb = s.submit(bad_W, good.C, good.p, islands=2, island_size=16, generations=3)
+        tg = s.submit(good.W, good.C, good.p, islands=2, island_size=16, generations=3)
+        res = {}
+        for _ in range(100):
+            s.step()
+            for t in (tb, tg):
+                if t in res:
+                    continue
+                try:
+                    r = s.poll(t)
+                except UsaphmpError as e:
+                    r = e
+                if r is not None:
+                    res[t] = r
+            if len(res) == 2:
+                break
+        assert isinstance(res[tb], UsaphmpError) and res[tb].name == "EINVAL"
+        assert isinstance(res[tg], dict)
