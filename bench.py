@@ -33,6 +33,10 @@ UNIT = "evals/s"
 WORKLOAD = "clustered n=1000 p=20, population 4096 (64 islands x 64), one GA generation per step"
 N, P_HUBS, ISLANDS, ISLAND = 1000, 20, 64, 64
 L2_FLUSH_BYTES = 512 << 20
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_eval_tc launch on this
+# workload, from the ncu capture summarised in profiles/k_eval_tc_clustered_n1000_p20.md
+# (None whenever the kernel has changed since that capture).
+K_EVAL_TC_DRAM_BYTES = 15139072
 REF_MEMBERS = 16
 
 
@@ -194,6 +198,55 @@ def e2e_eval(gi, inst, steps, warmup):
             "d2h_bytes_per_step": int(B * 8), "call": "usaphmp_eval (host hubs + S -> host fitness)"}
 
 
+def _make_request(r):
+    from paper_1704_06258_gb300 import synth
+    inst = synth.serving_request(r)
+    return inst.n, inst.p, inst.W, inst.C
+
+
+def serving_leg(n_requests, evals_per_s, seed=4242):
+    """Poisson arrivals of solve requests (n log-uniform in [50, 3000], p in 3..20,
+    population 512 = 8 x 64, 200 generations) into the continuous-batching
+    server; returns p50/p99 latency (arrival -> result) and throughput."""
+    import multiprocessing as mp
+    from paper_1704_06258_gb300 import synth
+    from paper_1704_06258_gb300.binding import PATH_SPLIT_BF16, Server
+    gens, R, P = 200, 8, 64
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 4)) as pool:
+        reqs = pool.map(_make_request, range(n_requests), chunksize=4)
+    # offered load: 80 % of the rate at which the GA runs these sizes alone
+    est_s = [gens * R * P * (n / N) ** 2 / evals_per_s for n, _, _, _ in reqs]
+    rate = 0.8 / float(np.mean(est_s))
+    arrivals = synth.poisson_arrivals(n_requests, rate, seed=seed)
+    lat, evals = [], 0
+    with Server(32 << 30, max_active=64, path=PATH_SPLIT_BF16) as srv:
+        t0 = time.perf_counter()
+        nxt, out = 0, {}
+        while nxt < n_requests or out:
+            now = time.perf_counter() - t0
+            while nxt < n_requests and arrivals[nxt] <= now:
+                n, p, W, C = reqs[nxt]
+                t = srv.submit(W, C, p, islands=R, island_size=P, generations=gens, seed=5000 + nxt)
+                out[t] = (arrivals[nxt], time.perf_counter() - t0)
+                nxt += 1
+            active, pending = srv.step()
+            for t in list(out):
+                r = srv.poll(t)
+                if r is not None:
+                    arr, sub = out.pop(t)
+                    lat.append(r["ms"] + (sub - arr) * 1e3)
+                    evals += r["evals"]
+            if not active and not pending and nxt < n_requests:
+                time.sleep(max(0.0, min(0.002, arrivals[nxt] - (time.perf_counter() - t0))))
+        makespan = time.perf_counter() - t0
+    lat = np.array(lat)
+    return {"requests": n_requests, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "evals_per_s": evals / makespan, "makespan_s": makespan,
+            "arrival_rate_per_s": rate, "population": R * P, "generations": gens, "max_active": 64,
+            "path": "split-bf16", "workload": "n log-uniform [50,3000], p uniform 3..20, clustered instances "
+                                              "seeded 5000+r, Poisson arrivals at 80% of the estimated capacity"}
+
+
 def run_ours(args):
     import torch
     from paper_1704_06258_gb300 import synth
@@ -210,13 +263,19 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     B = ISLANDS * ISLAND
     out = {}
+    only_split = args.legs == "split"
     with Instance.from_instance(inst) as gi:
-        gi.set_params(islands=ISLANDS, island_size=ISLAND, n1=10, path=PATH_PLAIN_FP32)
-        plain, plain_wall, _ = timed_generations(gi, max(3, args.steps // 2), args.warmup, flush, stream, world)
+        if not only_split:
+            gi.set_params(islands=ISLANDS, island_size=ISLAND, n1=10, path=PATH_PLAIN_FP32)
+            plain, _, _ = timed_generations(gi, max(3, args.steps // 4), args.warmup, flush, stream, world)
         gi.set_params(islands=ISLANDS, island_size=ISLAND, n1=10, path=PATH_SPLIT_BF16)
         with ClockSampler(local) as clk:
             split, wall, res = timed_generations(gi, args.steps, args.warmup, flush, stream, world)
-        e2e = e2e_eval(gi, inst, steps=max(3, args.steps // 4), warmup=1)
+        e2e = None if only_split else e2e_eval(gi, inst, steps=max(3, min(50, args.steps // 20)), warmup=1)
+    if only_split:
+        plain = dict(split)
+    ms0 = split["generation"]
+    serving = serving_leg(args.serve, B / (ms0 * 1e-3)) if (args.serve > 0 and world == 1 and not only_split) else None
     ms = max_over_ranks(split["generation"], world)
     value = B * world / (ms * 1e-3)
     plain_ms = max_over_ranks(plain["generation"], world)
@@ -240,8 +299,8 @@ def run_ours(args):
                    "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MB write, outside the step events)",
                    "parallelism": f"weak: one population per GPU x {world}"},
         "roofline": {"kernel": "k_eval_tc (transfer term)", "bound": "tensor", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
-                     "flops_per_launch": flops_per_launch, "avg_launch_ms": k1_ms},
+                     "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": peak_src,
+                     "traffic": K_EVAL_TC_DRAM_BYTES, "flops_per_launch": flops_per_launch, "avg_launch_ms": k1_ms},
         "cpu_baseline": cpu_baseline(inst) if (world == 1 and not args.no_cpu) else None,
         "e2e": e2e,
         "gpu_launches": 6 * args.steps,
@@ -250,6 +309,9 @@ def run_ours(args):
         "plain_fp32": {"value": B * world / (plain_ms * 1e-3), "ms_per_step": plain_ms,
                        "stage_ms": {k: round(v, 5) for k, v in plain.items()}},
         "split_vs_plain": plain_ms / ms,
+        "p50_solve_ms": serving["p50_ms"] if serving else None,
+        "p99_solve_ms": serving["p99_ms"] if serving else None,
+        "serving": serving,
         "best_cost_fp64": res["cost_fp64"], "best_cost_fp32": float(res["cost_fp32"]),
         "wall_s": wall,
     }
@@ -281,10 +343,13 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--serve", type=int, default=512, help="serving requests (0 = skip the serving leg)")
+    ap.add_argument("--legs", choices=["all", "split"], default="all",
+                    help="split: only the timed split-bf16 generations (for profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
