@@ -45,9 +45,21 @@ __global__ void __launch_bounds__(256) k_alloc(const __grid_constant__ TaskParam
       bl = 0;
       cih = CT[(long long)hs[0] * ldw + i];
       int own = (hs[0] == i) ? 0 : -1;
-      for (int l = 1; l < p; ++l) {
+      int l = 1;
+      // 8 loads in flight, then the compares in ascending hub order
+      for (; l + 8 <= p; l += 8) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldg(CT + (long long)hs[l + u] * ldw + i);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (v[u] < cih) { cih = v[u]; bl = l + u; }
+          if (hs[l + u] == i) own = l + u;
+        }
+      }
+      for (; l < p; ++l) {
         const int hl = hs[l];
-        const float v = CT[(long long)hl * ldw + i];
+        const float v = __ldg(CT + (long long)hl * ldw + i);
         if (v < cih) { cih = v; bl = l; }
         if (hl == i) own = l;
       }

@@ -141,14 +141,30 @@ __device__ __forceinline__ TileRef decode_tile(const TaskParam& tp, int g) {
   return r;
 }
 
-// 8 slot codes (two words) -> 8 bf16 values, 1.0 where the code equals l.
+// 0x80 in every byte of x that is zero, 0 elsewhere (no carry crosses a
+// byte: each byte's low 7 bits + 0x7F stays below 0x100).
+__device__ __forceinline__ uint32_t zero_byte_flags(uint32_t x) {
+  return ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) & 0x80808080u;
+}
+
+// prmt with sign replication: result byte k = 0xFF or 0x00, the top bit of
+// the source byte chosen by selector nibble k (bit 3 of the nibble set).
+__device__ __forceinline__ uint32_t prmt_sign(uint32_t x, uint32_t sel) {
+  uint32_t r;
+  asm("prmt.b32 %0, %1, 0, %2;" : "=r"(r) : "r"(x), "r"(sel));
+  return r;
+}
+
+// 8 slot codes (two words) -> 8 bf16 values, 1.0 (0x3F80) where the code
+// equals l (lrep = l in every byte), 0 elsewhere; element k goes to the k-th
+// 16-bit lane in memory order.
 __device__ __forceinline__ uint4 onehot8(uint32_t w0, uint32_t w1, uint32_t lrep) {
-  const uint32_t m0 = __vcmpeq4(w0, lrep), m1 = __vcmpeq4(w1, lrep);
+  const uint32_t z0 = zero_byte_flags(w0 ^ lrep), z1 = zero_byte_flags(w1 ^ lrep);
   uint4 o;
-  o.x = __byte_perm(m0, 0u, 0x1100) & 0x3F803F80u;
-  o.y = __byte_perm(m0, 0u, 0x3322) & 0x3F803F80u;
-  o.z = __byte_perm(m1, 0u, 0x1100) & 0x3F803F80u;
-  o.w = __byte_perm(m1, 0u, 0x3322) & 0x3F803F80u;
+  o.x = prmt_sign(z0, 0x9988u) & 0x3F803F80u;
+  o.y = prmt_sign(z0, 0xBBAAu) & 0x3F803F80u;
+  o.z = prmt_sign(z1, 0x9988u) & 0x3F803F80u;
+  o.w = prmt_sign(z1, 0xBBAAu) & 0x3F803F80u;
   return o;
 }
 
