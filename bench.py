@@ -103,27 +103,8 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def dist_setup():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
-
-
-def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-
-
-def max_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+from paper_1704_06258_gb300.dist import barrier, max_over_ranks, weak_scaling_value  # noqa: E402
+from paper_1704_06258_gb300.dist import world_info as dist_setup  # noqa: E402
 
 
 # ----------------------------------------------------------------- CPU oracle
@@ -277,7 +258,7 @@ def run_ours(args):
     ms0 = split["generation"]
     serving = serving_leg(args.serve, B / (ms0 * 1e-3)) if (args.serve > 0 and world == 1 and not only_split) else None
     ms = max_over_ranks(split["generation"], world)
-    value = B * world / (ms * 1e-3)
+    value = weak_scaling_value(B, split["generation"] * 1e-3, world)
     plain_ms = max_over_ranks(plain["generation"], world)
     peaks = load_peaks()
     flops_per_launch = 4.0 * N * N * P_HUBS * B      # 2 GEMMs (hi, lo) x 2 n^2 p per evaluation
