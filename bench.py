@@ -284,7 +284,7 @@ def run_ours(args):
                      "traffic": K_EVAL_TC_DRAM_BYTES, "flops_per_launch": flops_per_launch, "avg_launch_ms": k1_ms},
         "cpu_baseline": cpu_baseline(inst) if (world == 1 and not args.no_cpu) else None,
         "e2e": e2e,
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": 4 * args.steps,   # children, allocation, transfer, reduce+select
         "clocks": clk.summary(),
         "stage_ms": {k: round(v, 5) for k, v in split.items()},
         "plain_fp32": {"value": B * world / (plain_ms * 1e-3), "ms_per_step": plain_ms,

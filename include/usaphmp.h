@@ -157,8 +157,8 @@ int usaphmp_ga_result(usaphmp_t h, usaphmp_result* best, void* stream);
  * `stream` between the stages of every generation.  Synchronises `stream`
  * after each generation and adds the device time (ms) of each stage to
  * stage_ms[0..5]: 0 offspring (§4.1-4.2), 1 nearest allocation + access
- * terms, 2 transfer term (the configured evaluator), 3 fitness reduction,
- * 4 selection (§5), 5 the whole generation. */
+ * terms, 2 transfer term (the configured evaluator), 3 fitness reduction
+ * fused with selection (§5), 4 unused (0), 5 the whole generation. */
 int usaphmp_ga_run_profiled(usaphmp_t h, int32_t generations, void* stream, double* stage_ms);
 
 /* ---------------------------------------------------------------------------

@@ -76,7 +76,7 @@ _SIGS = {
     "usaphmp_server_destroy": (None, [c_vp]),
 }
 
-STAGES = ("offspring", "allocation", "transfer", "reduce", "select", "generation")
+STAGES = ("offspring", "allocation", "transfer", "reduce_select", "unused", "generation")
 
 _lib = None
 

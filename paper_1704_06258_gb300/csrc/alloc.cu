@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256) k_alloc(const __grid_constant__ TaskParam
       cih = CT[(long long)hs[bl] * ldw + i];
     }
     const float chi_i = sym ? cih : C[(long long)hs[bl] * ldw + i];  // C[h(i), i]
-    acc += chi * O[i] * cih + delta * D[i] * chi_i;
+    acc += access_term(chi, O[i], cih, delta, D[i], chi_i);
   }
   for (int i = n + threadIdx.x; i < ns; i += blockDim.x) slot[i] = kSlotPad;
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(T.pop.status, kStatusBadChromosome);

@@ -114,6 +114,7 @@ struct usaphmp_s {
   uint32_t* best = nullptr;
   float* best_fit = nullptr;
   int* gen = nullptr;
+  int* done = nullptr;
   uint32_t* mask0 = nullptr;
   Task ga_task{};
   bool ga_ready = false;
@@ -358,6 +359,9 @@ int ensure_ga(usaphmp_s* h) {
   RET(ensure_pop(h, h->one, 1));
   if (h->ga_R != R || h->ga_P != P || !h->anc) {
     dfree(h->anc); dfree(h->anc_fit); dfree(h->best); dfree(h->best_fit); dfree(h->gen); dfree(h->mask0);
+    dfree(h->done);
+    CK(dalloc(&h->done, 1));
+    CK(cudaMemset(h->done, 0, sizeof(int)));
     CK(dalloc(&h->anc, (size_t)R * h->nw));
     CK(dalloc(&h->anc_fit, (size_t)R));
     CK(dalloc(&h->best, (size_t)h->nw));
@@ -384,15 +388,19 @@ Task ga_task_of(usaphmp_s* h, unsigned long long seed) {
   t.ga.seed = seed;
   t.ga.gen = h->gen; t.ga.anc = h->anc; t.ga.anc_fit = h->anc_fit;
   t.ga.best = h->best; t.ga.best_fit = h->best_fit;
+  t.ga.done = h->done;
   return t;
 }
 
 int enqueue_generation(usaphmp_s* h, cudaStream_t s) {
   TaskSet ts{nullptr, &h->ga_task, 1};
   launch_children(ts, s);
-  CK(cudaGetLastError());
-  RET(run_eval(h, h->ga_task, true, s));
-  launch_select(ts, s);
+  launch_alloc(ts, true, use_tc(h), s);
+  if (use_tc(h))
+    launch_eval_tc(ts, h->num_sms, h->d_status, s);
+  else
+    launch_eval_plain(ts, s);
+  launch_reduce_select(ts, s);
   CK(cudaGetLastError());
   return USAPHMP_OK;
 }
@@ -455,6 +463,7 @@ void usaphmp_destroy(usaphmp_t h) {
   h->ev.release(); h->ga.release(); h->one.release();
   dfree(h->d_hubs_in); dfree(h->d_S_in); dfree(h->d_fit_out);
   dfree(h->anc); dfree(h->anc_fit); dfree(h->best); dfree(h->best_fit); dfree(h->gen); dfree(h->mask0);
+  dfree(h->done);
   if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -680,9 +689,8 @@ int usaphmp_ga_run_profiled(usaphmp_t h, int32_t generations, void* stream, doub
     else
       launch_eval_plain(ts, s);
     CK(cudaEventRecord(h->prof_ev[3], s));
-    launch_reduce(ts, s);
+    launch_reduce_select(ts, s);
     CK(cudaEventRecord(h->prof_ev[4], s));
-    launch_select(ts, s);
     CK(cudaEventRecord(h->prof_ev[5], s));
     CK(cudaGetLastError());
     CK(cudaEventSynchronize(h->prof_ev[5]));

@@ -33,6 +33,12 @@ enum : uint32_t {
 };
 
 __host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// One node's access terms chi*O_i*C[i,h(i)] + delta*D_i*C[h(i),i], written
+// with explicit roundings so that every kernel computes the same bits.
+__device__ __forceinline__ float access_term(float chi, float Oi, float cih, float delta, float Di, float chi_i) {
+  return __fmaf_rn(__fmul_rn(delta, Di), chi_i, __fmul_rn(__fmul_rn(chi, Oi), cih));
+}
 __host__ __device__ inline int chub_hstride(int p) { return p | 1; }
 __host__ __device__ inline int chub_cstride(int p) { return round_up(p * chub_hstride(p), 4); }
 
@@ -77,6 +83,7 @@ struct GaState {
   float* anc_fit;      // [R]
   uint32_t* best;      // [nw]
   float* best_fit;     // [1]
+  int* done;           // blocks finished in the fused selection (self-resetting)
 };
 
 struct Task {

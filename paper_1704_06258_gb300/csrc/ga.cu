@@ -287,6 +287,117 @@ __global__ void k_select_global(const __grid_constant__ TaskParam tp) {
   if (threadIdx.x == 0) *T.ga.gen = g + 1;
 }
 
+// Fitness reduction fused with selection, one block per island: the block
+// assembles its members' fitness (t12 + alpha * partials, fixed order),
+// replaces the island ancestor, and the last island block of the task to
+// finish (counted with an atomic after a fence) performs the best-ever
+// update, the merge every N1 generations and the generation increment -- the
+// same steps as k_reduce + k_select_islands + k_select_global.
+__global__ void __launch_bounds__(128) k_reduce_select(const __grid_constant__ TaskParam tp) {
+  __shared__ float sv[4];
+  __shared__ int si[4];
+  __shared__ int s_last, s_rb;
+  const int t = task_of(tp.bo, blockIdx.x);
+  const Task& T = task_at(tp, t);
+  const int r = blockIdx.x - tp.bo.o[t];
+  const int P = T.ga.P, R = T.ga.R, nw = T.in.nw, B = T.pop.B;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float v = INFINITY;
+  int idx = 0x7fffffff;
+  for (int j = threadIdx.x; j < P; j += blockDim.x) {
+    const int q = r * P + j;
+    const float* __restrict__ part = T.pop.part + q;
+    float s = 0.f;
+    for (int rr = 0; rr < T.pop.npart; ++rr) s += part[(long long)rr * B];
+    const float f = T.pop.t12[q] + T.in.alpha * s;
+    T.pop.fit[q] = f;
+    const float x = rank_key(f);
+    if (x < v || (x == v && j < idx)) { v = x; idx = j; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ov < v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+  }
+  if (lane == 0) { sv[wid] = v; si[wid] = idx; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      if (sv[w] < v || (sv[w] == v && si[w] < idx)) { v = sv[w]; idx = si[w]; }
+    sv[0] = v;
+    si[0] = idx;
+  }
+  __syncthreads();
+  v = sv[0];
+  idx = si[0];
+  const bool take = !(T.ga.elitist && !(v < T.ga.anc_fit[r]));
+  if (take) {
+    const uint32_t* src = T.pop.mask + (long long)(r * P + idx) * nw;
+    uint32_t* dst = T.ga.anc + (long long)r * nw;
+    for (int x = threadIdx.x; x < nw; x += blockDim.x) dst[x] = src[x];
+    if (threadIdx.x == 0) T.ga.anc_fit[r] = v;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(T.ga.done, 1) == R - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // global step (this block saw every island's update)
+  v = INFINITY;
+  idx = 0x7fffffff;
+  for (int rr = threadIdx.x; rr < R; rr += blockDim.x) {
+    const float x = rank_key(__ldcg(T.ga.anc_fit + rr));
+    if (x < v || (x == v && rr < idx)) { v = x; idx = rr; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ov < v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+  }
+  if (lane == 0) { sv[wid] = v; si[wid] = idx; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      if (sv[w] < v || (sv[w] == v && si[w] < idx)) { v = sv[w]; idx = si[w]; }
+    s_rb = idx;
+  }
+  __syncthreads();
+  const int rb = s_rb;
+  const float fb = __ldcg(T.ga.anc_fit + rb);
+  const uint32_t* src = T.ga.anc + (long long)rb * nw;
+  const bool improve = fb < *T.ga.best_fit;
+  __syncthreads();
+  if (improve) {
+    for (int x = threadIdx.x; x < nw; x += blockDim.x) T.ga.best[x] = __ldcg(src + x);
+    if (threadIdx.x == 0) *T.ga.best_fit = fb;
+  }
+  const int g = *T.ga.gen;
+  if ((g + 1) % T.ga.N1 == 0) {
+    for (long long e = threadIdx.x; e < (long long)R * nw; e += blockDim.x) {
+      const int rr = (int)(e / nw);
+      if (rr != rb) T.ga.anc[e] = __ldcg(src + (e - (long long)rr * nw));
+    }
+    for (int rr = threadIdx.x; rr < R; rr += blockDim.x)
+      if (rr != rb) T.ga.anc_fit[rr] = fb;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *T.ga.gen = g + 1;
+    *T.ga.done = 0;
+  }
+}
+
+void launch_reduce_select(const TaskSet& ts, cudaStream_t s) {
+  TaskParam tp = make_param(ts);
+  for (int t = 0; t < ts.count; ++t) tp.bo.o[t + 1] = tp.bo.o[t] + ts.h[t].ga.R;
+  const int blocks = tp.bo.o[ts.count];
+  if (blocks == 0) return;
+  k_reduce_select<<<blocks, 128, 0, s>>>(tp);
+}
+
 // Start state: every ancestor and the best-ever = the initial solution.
 __global__ void k_ga_init(const __grid_constant__ Task T, const uint32_t* __restrict__ mask0,
                           const float* __restrict__ fit0) {
@@ -298,7 +409,7 @@ __global__ void k_ga_init(const __grid_constant__ Task T, const uint32_t* __rest
     T.ga.anc_fit[r] = *fit0;
   if (blockIdx.x == 0) {
     for (int x = threadIdx.x; x < nw; x += blockDim.x) T.ga.best[x] = mask0[x];
-    if (threadIdx.x == 0) { *T.ga.best_fit = *fit0; *T.ga.gen = 0; }
+    if (threadIdx.x == 0) { *T.ga.best_fit = *fit0; *T.ga.gen = 0; *T.ga.done = 0; }
   }
 }
 

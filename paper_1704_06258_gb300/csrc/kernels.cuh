@@ -88,6 +88,9 @@ void launch_reduce(const TaskSet& ts, cudaStream_t s);
 // ga.cu: offspring (exchange, crossover, mutation, correction) and selection.
 void launch_children(const TaskSet& ts, cudaStream_t s);
 void launch_select(const TaskSet& ts, cudaStream_t s);
+// ga.cu: fitness reduction fused with selection (GA generations only).
+void launch_reduce_select(const TaskSet& ts, cudaStream_t s);
+
 // Start state of a single-task GA: ancestors and best-ever = mask0, fit0.
 void launch_ga_init(const Task& task, const uint32_t* mask0, const float* fit0, cudaStream_t s);
 

@@ -220,8 +220,7 @@ int usaphmp_server_step(usaphmp_server_t s, int32_t* n_active, int32_t* n_pendin
       launch_eval_tc(ts, s->num_sms, s->d_status, s->stream);
     else
       launch_eval_plain(ts, s->stream);
-    launch_reduce(ts, s->stream);
-    launch_select(ts, s->stream);
+    launch_reduce_select(ts, s->stream);
     e = cudaGetLastError();
     if (e != cudaSuccess) return report_error(USAPHMP_ECUDA, std::string("generation launch: ") + cudaGetErrorString(e));
     for (auto& r : s->active) {

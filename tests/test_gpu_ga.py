@@ -170,6 +170,48 @@ def test_ga_generations_replay_bit_exact(path):
 
 
 @pytest.mark.parametrize("path", [PATH_PLAIN_FP32, PATH_SPLIT_BF16], ids=["plain", "split"])
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_fused_generation_equals_step_chain(path, use_graph):
+    """The GA loop (fused reduction + selection, optionally graph-replayed)
+    gives the same state as the step-level kernels (separate reduction and
+    selection)."""
+    n, p, R, P, N1, seed, G = 230, 9, 4, 16, 3, 77, 8
+    inst = synth.clustered(seed=16, n=n, p=p)
+    B = R * P
+    with Instance.from_instance(inst) as gi:
+        gi.set_params(islands=R, island_size=P, n1=N1, path=path, use_graph=use_graph)
+        gi.ga_begin(seed, stream())
+        gi.ga_run(G, stream())
+        fused = gi.ga_result(stream())
+        # the same generations through the step-level entry points
+        hubs0 = cost.middle_nodes(inst.C, p).astype(np.int32)
+        m0 = np.isin(np.arange(n), hubs0)
+        d_h0 = dev(hubs0[None])
+        s0 = torch.zeros((1, gi.ns), dtype=torch.uint8, device="cuda")
+        f0 = torch.zeros(1, dtype=torch.float32, device="cuda")
+        gi.allocate_dev(1, d_h0.data_ptr(), s0.data_ptr(), stream())
+        gi.eval_slots_dev(1, d_h0.data_ptr(), s0.data_ptr(), f0.data_ptr(), stream())
+        fit0 = float(host(f0)[0])
+        d_anc = dev(pack_masks(np.tile(m0, (R, 1))).view(np.int32))
+        d_af = dev(np.full(R, fit0, np.float32))
+        d_best = dev(pack_masks(m0).view(np.int32)[0])
+        d_bf = dev(np.array([fit0], np.float32))
+        m = torch.zeros((B, gi.nw), dtype=torch.int32, device="cuda")
+        h = torch.zeros((B, p), dtype=torch.int32, device="cuda")
+        sl = torch.zeros((B, gi.ns), dtype=torch.uint8, device="cuda")
+        f = torch.zeros(B, dtype=torch.float32, device="cuda")
+        for g in range(G):
+            gi.children_dev(R, P, d_anc.data_ptr(), seed, g, m.data_ptr(), h.data_ptr(), stream())
+            gi.allocate_dev(B, h.data_ptr(), sl.data_ptr(), stream())
+            gi.eval_slots_dev(B, h.data_ptr(), sl.data_ptr(), f.data_ptr(), stream())
+            gi.select_dev(R, P, g, m.data_ptr(), f.data_ptr(), d_anc.data_ptr(), d_af.data_ptr(),
+                          d_best.data_ptr(), d_bf.data_ptr(), stream())
+        best = np.flatnonzero(unpack_masks(host(d_best).view(np.uint32)[None], n)[0])
+        np.testing.assert_array_equal(fused["hubs"], best)
+        assert fused["cost_fp32"] == host(d_bf)[0]
+
+
+@pytest.mark.parametrize("path", [PATH_PLAIN_FP32, PATH_SPLIT_BF16], ids=["plain", "split"])
 def test_solve_tiny_reaches_brute_force_nearest_optimum(path):
     inst = synth.tiny()
     bf = brute.brute_force(inst.W, inst.C, inst.chi, inst.alpha, inst.delta, inst.p)
