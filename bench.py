@@ -228,6 +228,58 @@ def serving_leg(n_requests, evals_per_s, seed=4242):
                                               "seeded 5000+r, Poisson arrivals at 80% of the estimated capacity"}
 
 
+def rel_error_sample(gi, inst, count=64, seed=99):
+    """Max relative error of each path's fitness against the library's fp64
+    rescoring (pair form of eq. 1) on `count` random chromosomes."""
+    import torch
+    from paper_1704_06258_gb300 import synth
+    from paper_1704_06258_gb300.binding import PATH_PLAIN_FP32, PATH_SPLIT_BF16
+    hubs, S = synth.random_population(seed, inst.n, inst.p, count)
+    hs = np.sort(hubs, axis=1).astype(np.int32)
+    rank = np.full((count, inst.n), 0, np.int64)
+    for b in range(count):
+        pos = {int(k): r for r, k in enumerate(hs[b])}
+        rank[b] = [pos[int(x)] for x in S[b]]
+    slot = np.full((count, gi.ns), 255, np.uint8)
+    slot[:, :inst.n] = rank
+    d_h, d_s = torch.from_numpy(hs).cuda(), torch.from_numpy(slot).cuda()
+    c64 = torch.empty(count, dtype=torch.float64, device="cuda")
+    gi.rescore_fp64_dev(count, d_h.data_ptr(), d_s.data_ptr(), c64.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    ref = c64.cpu().numpy()
+    out = {}
+    prm = gi.params
+    for name, path in (("plain_fp32", PATH_PLAIN_FP32), ("split_bf16", PATH_SPLIT_BF16)):
+        gi.set_params(path=path)
+        f = gi.eval(hubs, S)
+        out[name] = float(np.max(np.abs(f - ref) / ref))
+    gi.set_params(**prm)
+    return out
+
+
+def large_n_leg(steps, warmup, flush, stream):
+    """n=6000, p in {20, 50}, population 2048 (32 islands x 64): generations/s of
+    both evaluators on the uniform instance with 10% zero flows."""
+    from paper_1704_06258_gb300 import synth
+    from paper_1704_06258_gb300.binding import PATH_PLAIN_FP32, PATH_SPLIT_BF16, Instance
+    res = {}
+    for p in (20, 50):
+        inst = synth.large_uniform(p=p)
+        row = {}
+        with Instance.from_instance(inst) as gi:
+            for name, path in (("split_bf16", PATH_SPLIT_BF16), ("plain_fp32", PATH_PLAIN_FP32)):
+                gi.set_params(islands=32, island_size=64, n1=10, path=path)
+                st, _, _ = timed_generations(gi, steps, warmup, flush, stream, 1)
+                row[name] = {"evals_per_s": 2048 / (st["generation"] * 1e-3), "ms_per_step": st["generation"],
+                             "transfer_ms": st["transfer"]}
+                if name == "split_bf16":
+                    fl = 4.0 * inst.n * inst.n * p * 2048
+                    row[name]["tensor_tflops"] = fl / (st["transfer"] * 1e-3) / 1e12
+            row["rel_err_vs_fp64"] = rel_error_sample(gi, inst, count=8)
+        row["split_vs_plain"] = row["plain_fp32"]["ms_per_step"] / row["split_bf16"]["ms_per_step"]
+        res[f"n6000_p{p}"] = row
+    return res
+
+
 def run_ours(args):
     import torch
     from paper_1704_06258_gb300 import synth
@@ -253,6 +305,8 @@ def run_ours(args):
         with ClockSampler(local) as clk:
             split, wall, res = timed_generations(gi, args.steps, args.warmup, flush, stream, world)
         e2e = None if only_split else e2e_eval(gi, inst, steps=max(3, min(50, args.steps // 20)), warmup=1)
+        rel_err = None if only_split else rel_error_sample(gi, inst)
+    large = large_n_leg(20, 3, flush, stream) if (not only_split and world == 1 and args.large) else None
     if only_split:
         plain = dict(split)
     ms0 = split["generation"]
@@ -290,6 +344,8 @@ def run_ours(args):
         "plain_fp32": {"value": B * world / (plain_ms * 1e-3), "ms_per_step": plain_ms,
                        "stage_ms": {k: round(v, 5) for k, v in plain.items()}},
         "split_vs_plain": plain_ms / ms,
+        "rel_err_vs_fp64": rel_err,
+        "large_n": large,
         "p50_solve_ms": serving["p50_ms"] if serving else None,
         "p99_solve_ms": serving["p99_ms"] if serving else None,
         "serving": serving,
@@ -329,6 +385,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--serve", type=int, default=512, help="serving requests (0 = skip the serving leg)")
+    ap.add_argument("--large", type=int, default=1, help="also time the n=6000 configuration (0 = skip)")
     ap.add_argument("--legs", choices=["all", "split"], default="all",
                     help="split: only the timed split-bf16 generations (for profiling runs)")
     args = ap.parse_args()
