@@ -10,10 +10,11 @@
 //   slot          u8    [B][ns]    rank in `hubs` of the hub serving node i;
 //                                  ns = n rounded up to 64, padding = 0xFF
 //   chub          fp32  [B][cstride]  hub-to-hub costs of chromosome b:
-//                 chub[b][k * hstride + l] = C[hubs_b[k], hubs_b[l]], with
-//                 hstride = p rounded up to odd (bank-conflict-free rows) and
-//                 cstride = p * hstride rounded up to a multiple of 4 floats
-//                 (16-byte aligned blocks for bulk copies)
+//                 chub[b][k * hstride + l] = C[hubs_b[k], hubs_b[l]], rows of
+//                 hstride = 4 * (odd number) >= p floats: 16-byte aligned rows
+//                 whose 16-byte groups fall in distinct bank groups for
+//                 distinct k mod 8; cstride = p * hstride (aligned blocks for
+//                 bulk copies)
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -39,8 +40,8 @@ __host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m *
 __device__ __forceinline__ float access_term(float chi, float Oi, float cih, float delta, float Di, float chi_i) {
   return __fmaf_rn(__fmul_rn(delta, Di), chi_i, __fmul_rn(__fmul_rn(chi, Oi), cih));
 }
-__host__ __device__ inline int chub_hstride(int p) { return p | 1; }
-__host__ __device__ inline int chub_cstride(int p) { return round_up(p * chub_hstride(p), 4); }
+__host__ __device__ inline int chub_hstride(int p) { return 4 * (((p + 3) / 4) | 1); }
+__host__ __device__ inline int chub_cstride(int p) { return p * chub_hstride(p); }
 
 // Immutable per-instance device data.
 struct DevInst {

@@ -324,62 +324,44 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BNMAX);
       float* __restrict__ out = T.pop.part + (long long)(tr.m * 4 + quarter) * B + b0;
       const float* fbase = geo.slab ? slab : chub;
-      const int col_b = cb * p, col_e = ce * p;   // this warp's columns
-      constexpr int CH = 16;   // TMEM columns per chunk
-      const int k0 = col_b / CH, k1 = (col_e + CH - 1) / CH;
-      // running state at the first column of chunk k0: chromosome c, column l
-      int c = (k0 * CH) / p, l = k0 * CH - c * p;
-      float acc = 0.f;
-      for (int k = k0; k < k1; ++k) {
-        // factors chub_b[s_b(row)][l] of the chunk's columns, gathered
-        // branch-free: chromosome and slot indices are clamped to valid
-        // entries (the values of columns outside [col_b, col_e) are unused)
-        float f[CH];
-        {
-          int c2 = c, l2 = l;
-          if (use_tbl) {
+      // One chromosome at a time: its p accumulator columns (one TMEM column
+      // per load, any offset), the row's p factors chub_b[s_b(row)][0..p)
+      // as 16-byte vectors, one fma chain, one warp butterfly over the rows.
+      // Rows past n hold zeros (the TMA fills them), so they add nothing.
+      constexpr int LMAX = 32;
+      for (int c = cb; c < ce; ++c) {
+        const int sr = !rvalid ? 0
+                       : use_tbl ? min((int)tbl[c * 32 + lane], p - 1)
+                                 : min((int)__ldg(slot + (long long)c * ns + row), p - 1);
+        const float* frow = fbase + c * cst + sr * hst;
+        float acc = 0.f;
+        for (int l0 = 0; l0 < p; l0 += LMAX) {
+          const int nl = min(LMAX, p - l0);
+          uint32_t v[LMAX];
 #pragma unroll
-            for (int cc = 0; cc < CH; ++cc) {
-              const int cl = max(min(c2, ce - 1), 0);
-              const int sr = min((int)tbl[cl * 32 + lane], p - 1);
-              f[cc] = fbase[cl * cst + sr * hst + l2];
-              if (++l2 == p) { l2 = 0; ++c2; }
-            }
-          } else {
-#pragma unroll
-            for (int cc = 0; cc < CH; ++cc) {
-              const int cl = max(min(c2, ce - 1), 0);
-              const int sr = rvalid ? min((int)__ldg(slot + (long long)cl * ns + row), p - 1) : 0;
-              f[cc] = fbase[cl * cst + sr * hst + l2];
-              if (++l2 == p) { l2 = 0; ++c2; }
-            }
+          for (int l = 0; l < LMAX; ++l) {
+            v[l] = 0u;
+            if (l < nl) ptx::tmem_ld_32x1(taddr + (uint32_t)(c * p + l0 + l), v[l]);
           }
-        }
-        float v[CH];
-        ptx::tmem_ld_32x16(taddr + (uint32_t)(k * CH), v);
-        if (k + 1 == k1) {
-          ptx::tc_fence_before();
-          ptx::mbar_arrive(bars.tempty(buf));
-        }
+          float f[LMAX];
 #pragma unroll
-        for (int cc = 0; cc < CH; ++cc) {
-          const int col = k * CH + cc;
-          if (col >= col_b && col < col_e) {
-            acc = fmaf(v[cc], rvalid ? f[cc] : 0.f, acc);
-            if (l == p - 1) {
-#pragma unroll
-              for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-              if (lane == 0) out[c] = acc;
-              acc = 0.f;
-            }
+          for (int q = 0; q < LMAX / 4; ++q) {
+            float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (4 * q < nl) t = *reinterpret_cast<const float4*>(frow + l0 + 4 * q);
+            f[4 * q] = t.x; f[4 * q + 1] = t.y; f[4 * q + 2] = t.z; f[4 * q + 3] = t.w;
           }
-          if (++l == p) { l = 0; ++c; }
+          ptx::tmem_ld_wait32(v);
+#pragma unroll
+          for (int l = 0; l < LMAX; ++l)
+            if (l < nl) acc = fmaf(__uint_as_float(v[l]), f[l], acc);
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) out[c] = acc;
       }
-      if (k0 >= k1) {   // no chromosome for this warp: still release the accumulator
-        ptx::tc_fence_before();
-        ptx::mbar_arrive(bars.tempty(buf));
-      }
+      // every accumulator read of this warp has completed: release the buffer
+      ptx::tc_fence_before();
+      ptx::mbar_arrive(bars.tempty(buf));
       __syncwarp();
       if (lane == 0) ptx::mbar_arrive(bars.slab_empty());
     }
