@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(256) k_alloc(const __grid_constant__ TaskParam
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(T.pop.status, kStatusBadChromosome);
   const float s = block_sum(acc, red);
   if (threadIdx.x == 0) T.pop.t12[b] = s;
-  if (with_chub) {
+  if (with_chub || plain_global_table(p, T.in.ns)) {
     const int hst = chub_hstride(p), cst = chub_cstride(p);
     float* __restrict__ ch = T.pop.chub + (long long)b * cst;
     for (int e = threadIdx.x; e < cst; e += blockDim.x) {

@@ -43,6 +43,15 @@ __device__ __forceinline__ float access_term(float chi, float Oi, float cih, flo
 __host__ __device__ inline int chub_hstride(int p) { return 4 * (((p + 3) / 4) | 1); }
 __host__ __device__ inline int chub_cstride(int p) { return p * chub_hstride(p); }
 
+// The plain evaluator keeps one p x p hub-cost table and the slot codes of a
+// chromosome in shared memory; past this budget (p above about 220) it reads
+// the chromosome's chub rows from global memory instead, and the allocation
+// kernel writes them for every path.
+constexpr size_t kPlainSmemBudget = 200 * 1024;
+__host__ __device__ inline bool plain_global_table(int p, int ns) {
+  return (size_t)round_up(p * p * 4, 16) + (size_t)ns > kPlainSmemBudget;
+}
+
 // Immutable per-instance device data.
 struct DevInst {
   int n, p, ldw, ns, nw, symmetric;

@@ -37,7 +37,37 @@ inline int plain_kb(int p, int ns) {
 }
 
 inline size_t plain_smem(int kb, int p, int ns) {
+  if (plain_global_table(p, ns)) return (size_t)ns;  // kb is 1 then
   return (size_t)round_up(kb * p * p * 4, 16) + (size_t)kb * ns;
+}
+
+// One chromosome whose hub-cost table is too large for shared memory: the
+// same sums, gathering Chub_b[s_b(i)][s_b(j)] from its chub rows in global
+// memory (L2-resident, row stride hst).
+__device__ __forceinline__ float plain_global_sum(const float* __restrict__ W, const float* __restrict__ chub,
+                                                  const uint8_t* sl, int n, int ldw, int hst, int r0, int r1,
+                                                  int tpr, int G, int grp, int c4) {
+  float acc = 0.f;
+  for (int cb = c4; cb < ldw / 4; cb += tpr) {
+    const int j0 = cb * 4;
+    int cj[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) cj[c] = (j0 + c < n) ? (int)sl[j0 + c] : 0;
+    for (int i = r0 + grp; i < r1; i += 32 * G) {
+      float part = 0.f;
+      const int iend = min(r1, i + 32 * G);
+      for (int ii = i; ii < iend; ii += G) {
+        const float4 w = __ldg(reinterpret_cast<const float4*>(W + (long long)ii * ldw + j0));
+        const float* row = chub + (int)sl[ii] * hst;
+        part = fmaf(w.x, __ldg(row + cj[0]), part);
+        part = fmaf(w.y, __ldg(row + cj[1]), part);
+        part = fmaf(w.z, __ldg(row + cj[2]), part);
+        part = fmaf(w.w, __ldg(row + cj[3]), part);
+      }
+      acc += part;
+    }
+  }
+  return acc;
 }
 
 }  // namespace
@@ -55,13 +85,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_plain(const __grid_constan
   const int b0 = group * KB;
   const int nb = min(KB, B - b0);
   const int pp = p * p;
+  const bool gtab = KB == 1 && plain_global_table(p, ns);
   float* tab = reinterpret_cast<float*>(sm);
-  uint8_t* sl = sm + round_up(KB * pp * 4, 16);
+  uint8_t* sl = gtab ? sm : sm + round_up(KB * pp * 4, 16);
   const float* __restrict__ C = T.in.C;
   const float* __restrict__ W = T.in.W;
   const int32_t* __restrict__ hubs = T.pop.hubs;
 
-  for (int e = threadIdx.x; e < KB * pp; e += kThreads) {
+  for (int e = threadIdx.x; !gtab && e < KB * pp; e += kThreads) {
     const int bb = e / pp, r = e - bb * pp, k = r / p, l = r - k * p;
     float v = 0.f;
     if (bb < nb) {
@@ -91,8 +122,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_plain(const __grid_constan
   float acc[KB];
 #pragma unroll
   for (int bb = 0; bb < KB; ++bb) acc[bb] = 0.f;
+  if (gtab)
+    acc[0] = plain_global_sum(W, T.pop.chub + (long long)b0 * chub_cstride(p), sl, n, ldw, chub_hstride(p), r0, r1,
+                              tpr, G, grp, c4);
 
-  for (int cb = c4; cb < cols4; cb += tpr) {
+  for (int cb = c4; !gtab && cb < cols4; cb += tpr) {
     const int j0 = cb * 4;
     int coff[KB][4];
 #pragma unroll

@@ -20,8 +20,9 @@
 //     butterfly adds the 32 rows; one partial per (32-row group, chromosome)
 //     is written, D itself never leaves the SM.
 // Persistent kernel, one CTA per SM, warp roles: 0 TMA, 1 MMA (+ TMEM
-// allocation), 4-11 epilogue (warp w reads TMEM lane quarter w%4 and one half
-// of the tile's chromosomes), 12-19 one-hot producers.  Tiles are 128 rows x N columns x 64-deep K blocks, three
+// allocation), 2-9 epilogue (warp w reads TMEM lane quarter w%4 and one half
+// of the tile's chromosomes), 10-17 one-hot producers.  Tiles are 128 rows x
+// N columns x 64-deep K blocks, three
 // shared-memory stages, two TMEM accumulators (2 x 256 columns) so the
 // epilogue of one tile overlaps the MMAs of the next.  Every wait is bounded:
 // after kTimeoutNs the kernel raises kStatusTimeout, drains its own copies
@@ -35,9 +36,9 @@ namespace usaphmp {
 namespace {
 
 constexpr int BM = 128, BNMAX = 256, BK = 64, STAGES = 3;
-constexpr int kThreads = 640;
-constexpr int kEpiWarps = 8;
-constexpr int kProdWarp0 = 4 + kEpiWarps;
+constexpr int kEpiWarp0 = 2, kEpiWarps = 8;
+constexpr int kProdWarp0 = kEpiWarp0 + kEpiWarps;
+constexpr int kThreads = 32 * (kProdWarp0 + 8);
 constexpr uint32_t A_BYTES = BM * BK * 2;                 // 16 KB
 constexpr uint32_t B_BYTES = BNMAX * BK * 2;              // 32 KB
 constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + B_BYTES;   // 64 KB
@@ -67,7 +68,7 @@ struct Bars {
 
 // Single-thread bounded wait.  Returns false on timeout or when another role
 // has already aborted.
-__device__ bool wait_one(uint32_t bar, uint32_t parity, volatile int* abort_flag, uint32_t* status) {
+__device__ __forceinline__ bool wait_one(uint32_t bar, uint32_t parity, volatile int* abort_flag, uint32_t* status) {
   if (ptx::mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = ptx::globaltimer();
   for (uint32_t i = 1;; ++i) {
@@ -91,7 +92,7 @@ __device__ void wait_drain(uint32_t bar, uint32_t parity) {
 }
 
 // Warp-collective bounded wait: every lane returns the same answer.
-__device__ bool wait_warp(uint32_t bar, uint32_t parity, volatile int* abort_flag, uint32_t* status) {
+__device__ __forceinline__ bool wait_warp(uint32_t bar, uint32_t parity, volatile int* abort_flag, uint32_t* status) {
   const uint64_t t0 = ptx::globaltimer();
   for (uint32_t i = 0;; ++i) {
     const bool ok = ptx::mbar_try_wait(bar, parity);
@@ -155,22 +156,106 @@ __device__ __forceinline__ uint32_t prmt_sign(uint32_t x, uint32_t sel) {
   return r;
 }
 
-// 8 slot codes (two words) -> 8 bf16 values, 1.0 (0x3F80) where the code
-// equals l (lrep = l in every byte), 0 elsewhere; element k goes to the k-th
-// 16-bit lane in memory order.
+// The one-hot operand holds kOneHot = 2.0 (bf16 0x4000: a zero low byte) in
+// place of 1.0; every accumulator is then exactly twice M_b = W A_b and the
+// epilogue scales the chromosome's sum back by kOneHotInv (exact in fp32).
+constexpr float kOneHotInv = 0.5f;
+
+// 8 slot codes (two words) -> 8 bf16 values, kOneHot where the code equals l
+// (lrep = l in every byte), 0 elsewhere; element k goes to the k-th 16-bit
+// lane in memory order.  Exact equality test for every code and l.
 __device__ __forceinline__ uint4 onehot8(uint32_t w0, uint32_t w1, uint32_t lrep) {
   const uint32_t z0 = zero_byte_flags(w0 ^ lrep), z1 = zero_byte_flags(w1 ^ lrep);
   uint4 o;
-  o.x = prmt_sign(z0, 0x9988u) & 0x3F803F80u;
-  o.y = prmt_sign(z0, 0xBBAAu) & 0x3F803F80u;
-  o.z = prmt_sign(z1, 0x9988u) & 0x3F803F80u;
-  o.w = prmt_sign(z1, 0xBBAAu) & 0x3F803F80u;
+  o.x = prmt_sign(z0, 0x9988u) & 0x40004000u;
+  o.y = prmt_sign(z0, 0xBBAAu) & 0x40004000u;
+  o.z = prmt_sign(z1, 0x9988u) & 0x40004000u;
+  o.w = prmt_sign(z1, 0xBBAAu) & 0x40004000u;
+  return o;
+}
+
+// 0x40 in every byte of w that equals l, when every code is below 63 or the
+// pad 0xFF and l <= 62 (p <= 63): the byte y = code ^ l is then in [0, 0x3F]
+// or [0xC1, 0xFF], (y | 0x40) - 1 borrows from no byte and clears bit 6
+// exactly when y == 0.
+__device__ __forceinline__ uint32_t eq_flags40(uint32_t w, uint32_t lrep) {
+  return ~(((w ^ lrep) | 0x40404040u) - 0x01010101u) & 0x40404040u;
+}
+
+// onehot8 for p <= 63: the flag byte is already the high byte of kOneHot.
+__device__ __forceinline__ uint4 onehot8_small(uint32_t w0, uint32_t w1, uint32_t lrep) {
+  const uint32_t f0 = eq_flags40(w0, lrep), f1 = eq_flags40(w1, lrep);
+  uint4 o;
+  asm("prmt.b32 %0, %1, 0, 0x1404;" : "=r"(o.x) : "r"(f0));
+  asm("prmt.b32 %0, %1, 0, 0x3424;" : "=r"(o.y) : "r"(f0));
+  asm("prmt.b32 %0, %1, 0, 0x1404;" : "=r"(o.z) : "r"(f1));
+  asm("prmt.b32 %0, %1, 0, 0x3424;" : "=r"(o.w) : "r"(f1));
   return o;
 }
 
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint4 v) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
                : "memory");
+}
+
+struct EpiArgs {
+  uint32_t taddr;
+  int cb, ce, p, hst, cst, ns, row, lane;
+  bool rvalid, use_tbl;
+  const uint8_t* tbl;
+  const uint8_t* slot;
+  const float* fbase;
+  float* out;
+};
+
+// Epilogue of one warp over its chromosomes [cb, ce), one at a time: the p
+// accumulator columns of the chromosome (TMEM loads of WID columns), the
+// row's p factors Chub_b[s_b(row)][0..p) as 16-byte vectors, one fma chain
+// and a warp butterfly over the 32 rows.  Rows past n hold zeros (the TMA
+// fills them), so they add nothing.
+template <int WID>
+__device__ __forceinline__ void epi_chromosomes(const EpiArgs& a) {
+  constexpr int LMAX = 32;
+  const int p = a.p;
+  for (int c = a.cb; c < a.ce; ++c) {
+    const int sr = !a.rvalid ? 0
+                   : a.use_tbl ? min((int)a.tbl[c * 32 + a.lane], p - 1)
+                               : min((int)__ldg(a.slot + (long long)c * a.ns + a.row), p - 1);
+    const float* frow = a.fbase + c * a.cst + sr * a.hst;
+    float acc = 0.f;
+    for (int l0 = 0; l0 < p; l0 += LMAX) {
+      const int nl = min(LMAX, p - l0);
+      uint32_t v[LMAX];
+#pragma unroll
+      for (int l = 0; l < LMAX; ++l) v[l] = 0u;
+      const uint32_t ta = a.taddr + (uint32_t)(c * p + l0);
+#pragma unroll
+      for (int l = 0; l < LMAX; l += WID) {
+        if (l < nl) {
+          if constexpr (WID == 4)
+            ptx::tmem_ld_32x4(ta + l, v[l], v[l + 1], v[l + 2], v[l + 3]);
+          else if constexpr (WID == 2)
+            ptx::tmem_ld_32x2(ta + l, v[l], v[l + 1]);
+          else
+            ptx::tmem_ld_32x1(ta + l, v[l]);
+        }
+      }
+      ptx::tmem_ld_wait32(v);
+#pragma unroll
+      for (int q = 0; q < LMAX / 4; ++q) {
+        if (4 * q < nl) {
+          const float4 t = *reinterpret_cast<const float4*>(frow + l0 + 4 * q);
+          acc = fmaf(__uint_as_float(v[4 * q]), t.x, acc);
+          if (4 * q + 1 < nl) acc = fmaf(__uint_as_float(v[4 * q + 1]), t.y, acc);
+          if (4 * q + 2 < nl) acc = fmaf(__uint_as_float(v[4 * q + 2]), t.z, acc);
+          if (4 * q + 3 < nl) acc = fmaf(__uint_as_float(v[4 * q + 3]), t.w, acc);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (a.lane == 0) a.out[c] = acc * kOneHotInv;
+  }
 }
 
 }  // namespace
@@ -267,9 +352,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     ptx::tc_commit(bars.drain());
     wait_drain(bars.drain(), 0);
-  } else if (warp >= 4 && warp < 4 + kEpiWarps) {
+  } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + kEpiWarps) {
     // --------------------------------------------------------------- epilogue
-    const int quarter = warp & 3, half = (warp - 4) >> 2;
+    const int quarter = warp & 3, half = (warp - kEpiWarp0) >> 2;
     uint8_t* tbl = sm + kTblOffset + quarter * (kTblChrom * 32);
     const float* slab = reinterpret_cast<const float*>(sm + kSlabOffset);
     int tl = 0;
@@ -291,7 +376,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int cb = half ? split : 0, ce = half ? nchrom : split;
       // Chub tables of the tile's chromosomes -> slab (single buffer, one
       // bulk copy issued once every epilogue warp has released the slab).
-      if (warp == 4 && lane == 0) {
+      if (warp == kEpiWarp0 && lane == 0) {
         if (wait_one(bars.slab_empty(), (uint32_t)(tl & 1) ^ 1u, abort_flag, status)) {
           if (geo.slab) {
             const uint32_t bytes = (uint32_t)(nchrom * cst * 4);
@@ -324,41 +409,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BNMAX);
       float* __restrict__ out = T.pop.part + (long long)(tr.m * 4 + quarter) * B + b0;
       const float* fbase = geo.slab ? slab : chub;
-      // One chromosome at a time: its p accumulator columns (one TMEM column
-      // per load, any offset), the row's p factors chub_b[s_b(row)][0..p)
-      // as 16-byte vectors, one fma chain, one warp butterfly over the rows.
-      // Rows past n hold zeros (the TMA fills them), so they add nothing.
-      constexpr int LMAX = 32;
-      for (int c = cb; c < ce; ++c) {
-        const int sr = !rvalid ? 0
-                       : use_tbl ? min((int)tbl[c * 32 + lane], p - 1)
-                                 : min((int)__ldg(slot + (long long)c * ns + row), p - 1);
-        const float* frow = fbase + c * cst + sr * hst;
-        float acc = 0.f;
-        for (int l0 = 0; l0 < p; l0 += LMAX) {
-          const int nl = min(LMAX, p - l0);
-          uint32_t v[LMAX];
-#pragma unroll
-          for (int l = 0; l < LMAX; ++l) {
-            v[l] = 0u;
-            if (l < nl) ptx::tmem_ld_32x1(taddr + (uint32_t)(c * p + l0 + l), v[l]);
-          }
-          float f[LMAX];
-#pragma unroll
-          for (int q = 0; q < LMAX / 4; ++q) {
-            float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (4 * q < nl) t = *reinterpret_cast<const float4*>(frow + l0 + 4 * q);
-            f[4 * q] = t.x; f[4 * q + 1] = t.y; f[4 * q + 2] = t.z; f[4 * q + 3] = t.w;
-          }
-          ptx::tmem_ld_wait32(v);
-#pragma unroll
-          for (int l = 0; l < LMAX; ++l)
-            if (l < nl) acc = fmaf(__uint_as_float(v[l]), f[l], acc);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) out[c] = acc;
-      }
+      // one code path per TMEM load width (the widest that keeps every
+      // column offset c*p + l aligned)
+      const EpiArgs ea{taddr, cb, ce, p, hst, cst, ns, row, lane, rvalid, use_tbl, tbl, slot, fbase, out};
+      if ((p & 3) == 0)
+        epi_chromosomes<4>(ea);
+      else if ((p & 1) == 0)
+        epi_chromosomes<2>(ea);
+      else
+        epi_chromosomes<1>(ea);
       // every accumulator read of this warp has completed: release the buffer
       ptx::tc_fence_before();
       ptx::mbar_arrive(bars.tempty(buf));
@@ -381,6 +440,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int nk = (n + BK - 1) / BK;
       const bool valid = r < nchrom * p;   // rows in [nchrom*p, nmma) are zero
       const bool write = r < nmma;
+      const bool small = p <= 63;
       const int c = valid ? r / p : 0;
       const uint32_t lrep = (uint32_t)(valid ? r - c * p : 0) * 0x01010101u;
       const uint8_t* srow = T.pop.slot + (long long)(b0 + c) * ns;
@@ -400,7 +460,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
         if (!(ok = wait_warp(bars.empty(s), ph ^ 1u, abort_flag, status))) break;
         const uint32_t dst = base + s * STAGE_BYTES + 2 * A_BYTES + (uint32_t)r * 128u;
-        if (valid) {
+        if (valid && small) {
+          st_shared_v4(dst + ((0u ^ swz) << 4), onehot8_small(q0.x, q0.y, lrep));
+          st_shared_v4(dst + ((1u ^ swz) << 4), onehot8_small(q0.z, q0.w, lrep));
+          st_shared_v4(dst + ((2u ^ swz) << 4), onehot8_small(q1.x, q1.y, lrep));
+          st_shared_v4(dst + ((3u ^ swz) << 4), onehot8_small(q1.z, q1.w, lrep));
+          st_shared_v4(dst + ((4u ^ swz) << 4), onehot8_small(q2.x, q2.y, lrep));
+          st_shared_v4(dst + ((5u ^ swz) << 4), onehot8_small(q2.z, q2.w, lrep));
+          st_shared_v4(dst + ((6u ^ swz) << 4), onehot8_small(q3.x, q3.y, lrep));
+          st_shared_v4(dst + ((7u ^ swz) << 4), onehot8_small(q3.z, q3.w, lrep));
+        } else if (valid) {
           st_shared_v4(dst + ((0u ^ swz) << 4), onehot8(q0.x, q0.y, lrep));
           st_shared_v4(dst + ((1u ^ swz) << 4), onehot8(q0.z, q0.w, lrep));
           st_shared_v4(dst + ((2u ^ swz) << 4), onehot8(q1.x, q1.y, lrep));

@@ -35,6 +35,11 @@ CASES = {
     "n333_p7_ragged": lambda: synth.urand200(seed=77, n=333, p=7),
     "n257_p1": lambda: synth.urand200(seed=78, n=257, p=1),
     "n129_p64": lambda: synth.urand200(seed=79, n=129, p=64),
+    "n140_p50": lambda: synth.urand200(seed=83, n=140, p=50),
+    "n300_p63": lambda: synth.urand200(seed=81, n=300, p=63),
+    "n260_p100": lambda: synth.urand200(seed=82, n=260, p=100),
+    "n240_p226_plain_smem_edge": lambda: synth.urand200(seed=84, n=240, p=226),
+    "n300_p255_max": lambda: synth.urand200(seed=85, n=300, p=255),
     "asym_n150_p6": lambda: asym_instance(80, 150, 6),
 }
 
