@@ -36,7 +36,9 @@ L2_FLUSH_BYTES = 512 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_eval_tc launch on this
 # workload, from the ncu capture summarised in profiles/k_eval_tc_clustered_n1000_p20.md
 # (None whenever the kernel has changed since that capture).
-K_EVAL_TC_DRAM_BYTES = None
+K_EVAL_TC_DRAM_BYTES = 14802176
+# the same for one k_alloc launch (profiles/k_alloc_clustered_n1000_p20.md)
+K_ALLOC_DRAM_BYTES = 4349440
 REF_MEMBERS = 16
 
 
@@ -256,6 +258,17 @@ def rel_error_sample(gi, inst, count=64, seed=99):
     return out
 
 
+def alloc_bytes(n, p, B):
+    """Algorithmic bytes of one allocation launch (nearest allocation, access
+    terms, hub-cost tables) over B chromosomes: per chromosome the hub ids,
+    the p hub rows of C (p*n floats), O and D, the slot codes written, t12,
+    the p*p hub-to-hub costs read and the padded table written."""
+    ns = -(-n // 64) * 64
+    hst = 4 * ((((p + 3) // 4)) | 1)
+    per = 4 * p + 4 * p * n + 8 * n + ns + 4 + 4 * p * p + 4 * p * hst
+    return per * B
+
+
 def large_n_leg(steps, warmup, flush, stream):
     """n=6000, p in {20, 50}, population 2048 (32 islands x 64): generations/s of
     both evaluators on the uniform instance with 10% zero flows."""
@@ -274,6 +287,8 @@ def large_n_leg(steps, warmup, flush, stream):
                 if name == "split_bf16":
                     fl = 4.0 * inst.n * inst.n * p * 2048
                     row[name]["tensor_tflops"] = fl / (st["transfer"] * 1e-3) / 1e12
+                    row[name]["alloc_ms"] = st["allocation"]
+                    row[name]["alloc_gbs"] = alloc_bytes(inst.n, p, 2048) / (st["allocation"] * 1e-3) / 1e9
             row["rel_err_vs_fp64"] = rel_error_sample(gi, inst, count=8)
         row["split_vs_plain"] = row["plain_fp32"]["ms_per_step"] / row["split_bf16"]["ms_per_step"]
         res[f"n6000_p{p}"] = row
@@ -322,6 +337,10 @@ def run_ours(args):
         peak, peak_src = peaks["bf16_tflops_sustained"], "measured bf16 sustained (MEASURED_PEAKS.json)"
     else:
         peak, peak_src = 1700.0, "fallback sustained bf16"
+    a_bytes = alloc_bytes(N, P_HUBS, B)
+    a_ms = split["allocation"]
+    hbm = (peaks or {}).get("hbm_gbs") or 6800.0
+    hbm_src = "measured HBM copy (MEASURED_PEAKS.json)" if (peaks or {}).get("hbm_gbs") else "fallback HBM"
     if rank != 0:
         return
     line = {
@@ -336,6 +355,12 @@ def run_ours(args):
         "roofline": {"kernel": "k_eval_tc (transfer term)", "bound": "tensor", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": peak_src,
                      "traffic": K_EVAL_TC_DRAM_BYTES, "flops_per_launch": flops_per_launch, "avg_launch_ms": k1_ms},
+        "roofline_gather": {"kernel": "k_alloc (nearest allocation + access terms + hub-cost tables)",
+                            "bound": "hbm", "achieved": a_bytes / (a_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                            "frac": a_bytes / (a_ms * 1e-3) / 1e9 / hbm, "peak_source": hbm_src,
+                            "traffic": K_ALLOC_DRAM_BYTES, "bytes_per_launch": a_bytes, "avg_launch_ms": a_ms,
+                            "note": "C (4 MB) stays in L2 at n=1000, so the algorithmic bytes are L2-served; "
+                                    "see large_n for the n=6000 case where C (144 MB) exceeds L2"},
         "cpu_baseline": cpu_baseline(inst) if (world == 1 and not args.no_cpu) else None,
         "e2e": e2e,
         "gpu_launches": 4 * args.steps,   # children, allocation, transfer, reduce+select
