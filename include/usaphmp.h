@@ -43,7 +43,8 @@ enum {
   USAPHMP_ENOMEM = -3,        /* device allocation failed */
   USAPHMP_ECUDA = -4,         /* a CUDA call failed (message names it) */
   USAPHMP_ETIMEOUT = -5,      /* a device-side wait gave up (kernel returned early) */
-  USAPHMP_EBUSY = -6          /* resource limit reached (admission refused) */
+  USAPHMP_EBUSY = -6,         /* resource limit reached (admission refused) */
+  USAPHMP_EIO = -7            /* a file could not be written */
 };
 
 /* Evaluators of the transfer term. */
@@ -194,6 +195,63 @@ int usaphmp_server_poll(usaphmp_server_t s, int64_t ticket, usaphmp_result* out)
 int usaphmp_server_footprint(int32_t n, int32_t p, int32_t islands, int32_t island_size, int64_t* bytes);
 
 void usaphmp_server_destroy(usaphmp_server_t s);
+
+/* ---------------------------------------------------------------------------
+ * Tile shapes of the tensor-core evaluator and their autotuner.  The paper
+ * has no counterpart (its kernel is one thread per chromosome).
+ *
+ * The split-bf16 evaluator (USAPHMP_PATH_SPLIT_BF16) multiplies W by the
+ * one-hot allocation matrices of the population in tiles of 128 rows x
+ * ntile columns; a tile holds floor(ntile / p) whole chromosomes.  Shape:
+ *   ntile   64, 128 or 256 (>= p)
+ *   stages  2..4 shared-memory pipeline stages (ntile 256: at most 3)
+ *   raster  0: the persistent CTAs walk the column tiles of one row block of
+ *           W first; 1: the row blocks of one column tile first.
+ * The shape changes speed only: fitness values are bit-identical for every
+ * shape.  Default {256, 3, 0}.  A handle's shape applies to its own
+ * evaluations and generations; the server uses the default. */
+typedef struct {
+  int32_t ntile;
+  int32_t stages;
+  int32_t raster;
+} usaphmp_tile;
+
+/* USAPHMP_EINVAL (nothing changed) for a shape outside the list above or
+ * with ntile < p.  Drops the handle's captured generation graph. */
+int usaphmp_set_tile(usaphmp_t h, const usaphmp_tile* tile);
+int usaphmp_get_tile(usaphmp_t h, usaphmp_tile* tile);
+
+/* Autotuner: times every valid shape on the handle's current population
+ * size (islands * island_size chromosomes of the handle's instance) and
+ * keeps the fastest as the handle's shape (ties keep the earlier candidate;
+ * the default is tried first).  Each candidate runs 1 untimed and `reps`
+ * timed launches (1 <= reps <= 1000) of the transfer-term kernel, measured
+ * with CUDA events on the handle's stream.  The population is one GA
+ * generation grown from the initial solution with a fixed seed, so the call
+ * resets the GA state: call usaphmp_ga_begin (or usaphmp_solve) afterwards.
+ * With cache_path non-NULL the bucket (device name, ceil(n/128), p, the
+ * population size rounded up to a power of two) is first looked up in that
+ * JSON file (format: usaphmp_tile_cache_store) and, when present and valid
+ * for p, applied without timing (*from_cache = 1); otherwise the timed
+ * choice is stored there.  Outputs may be NULL: the chosen shape, its mean
+ * launch time and the default shape's (both 0 when taken from the cache).
+ * On the plain path the call only returns the current shape. */
+int usaphmp_autotune(usaphmp_t h, int32_t reps, const char* cache_path, usaphmp_tile* chosen,
+                     double* chosen_ms, double* default_ms, int32_t* from_cache);
+
+/* The autotuner's JSON cache, host only (no GPU needed).  A file holds
+ *   {"format": "usaphmp-tile-cache-1", "entries": [{"device": "...",
+ *    "n_blocks": ceil(n/128), "p": p, "B_pow2": B rounded up to a power of
+ *    two, "ntile": ..., "stages": ..., "raster": ..., "ms": ...}, ...]}.
+ * lookup: 1 and *out (and *ms if non-NULL) filled when the bucket of
+ * (device, n, p, B) is present, 0 when it is not or the file does not exist,
+ * USAPHMP_EINVAL when the file is not such a JSON document.
+ * store: inserts or replaces the bucket's entry, rewriting the file through
+ * a temporary file and a rename (USAPHMP_EIO when that fails). */
+int usaphmp_tile_cache_lookup(const char* path, const char* device, int32_t n, int32_t p, int32_t B,
+                              usaphmp_tile* out, double* ms);
+int usaphmp_tile_cache_store(const char* path, const char* device, int32_t n, int32_t p, int32_t B,
+                             const usaphmp_tile* tile, double ms);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free entry point.  The paper has no counterpart: this exists for

@@ -21,7 +21,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "usaphmp.h")
 PATH_PLAIN_FP32 = 0
 PATH_SPLIT_BF16 = 1
 
-ERRORS = {-1: "EINVAL", -2: "EINVAL_CHROM", -3: "ENOMEM", -4: "ECUDA", -5: "ETIMEOUT", -6: "EBUSY"}
+ERRORS = {-1: "EINVAL", -2: "EINVAL_CHROM", -3: "ENOMEM", -4: "ECUDA", -5: "ETIMEOUT", -6: "EBUSY", -7: "EIO"}
 
 c_i32, c_i64, c_u64, c_f64, c_f32, c_vp = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
                                            ctypes.c_double, ctypes.c_float, ctypes.c_void_p)
@@ -35,6 +35,10 @@ class Params(ctypes.Structure):
 class Result(ctypes.Structure):
     _fields_ = [("hubs", ctypes.POINTER(c_i32)), ("S", ctypes.POINTER(c_i32)), ("cost_fp64", c_f64),
                 ("cost_fp32", c_f32), ("evals", c_i64), ("ms", c_f64)]
+
+
+class Tile(ctypes.Structure):
+    _fields_ = [("ntile", c_i32), ("stages", c_i32), ("raster", c_i32)]
 
 
 class UsaphmpError(RuntimeError):
@@ -74,6 +78,14 @@ _SIGS = {
     "usaphmp_server_poll": (c_i32, [c_vp, c_i64, ctypes.POINTER(Result)]),
     "usaphmp_server_footprint": (c_i32, [c_i32, c_i32, c_i32, c_i32, ctypes.POINTER(c_i64)]),
     "usaphmp_server_destroy": (None, [c_vp]),
+    "usaphmp_set_tile": (c_i32, [c_vp, ctypes.POINTER(Tile)]),
+    "usaphmp_get_tile": (c_i32, [c_vp, ctypes.POINTER(Tile)]),
+    "usaphmp_autotune": (c_i32, [c_vp, c_i32, ctypes.c_char_p, ctypes.POINTER(Tile), ctypes.POINTER(c_f64),
+                                 ctypes.POINTER(c_f64), ctypes.POINTER(c_i32)]),
+    "usaphmp_tile_cache_lookup": (c_i32, [ctypes.c_char_p, ctypes.c_char_p, c_i32, c_i32, c_i32,
+                                          ctypes.POINTER(Tile), ctypes.POINTER(c_f64)]),
+    "usaphmp_tile_cache_store": (c_i32, [ctypes.c_char_p, ctypes.c_char_p, c_i32, c_i32, c_i32,
+                                         ctypes.POINTER(Tile), c_f64]),
 }
 
 STAGES = ("offspring", "allocation", "transfer", "reduce_select", "unused", "generation")
@@ -115,6 +127,30 @@ def rescore_fp64_noalloc(n, p, B, W_ptr, C_ptr, chi, alpha, delta, hubs_ptr, slo
     """usaphmp_rescore_fp64_noalloc: no handle, no allocation (dense W, C, slot)."""
     check(lib().usaphmp_rescore_fp64_noalloc(n, p, B, W_ptr, C_ptr, chi, alpha, delta, hubs_ptr, slot_ptr,
                                              cost_ptr, stream))
+
+
+def _tile_dict(t):
+    return {"ntile": int(t.ntile), "stages": int(t.stages), "raster": int(t.raster)}
+
+
+def tile_cache_lookup(path, device, n, p, B):
+    """usaphmp_tile_cache_lookup: the cached tile dict (with "ms") or None."""
+    t, ms = Tile(), c_f64()
+    rc = lib().usaphmp_tile_cache_lookup(os.fsencode(path), device.encode(), n, p, B, ctypes.byref(t),
+                                         ctypes.byref(ms))
+    if rc < 0:
+        check(rc)
+    if rc == 0:
+        return None
+    d = _tile_dict(t)
+    d["ms"] = ms.value
+    return d
+
+
+def tile_cache_store(path, device, n, p, B, ntile, stages, raster, ms):
+    """usaphmp_tile_cache_store."""
+    t = Tile(ntile, stages, raster)
+    check(lib().usaphmp_tile_cache_store(os.fsencode(path), device.encode(), n, p, B, ctypes.byref(t), ms))
 
 
 class Instance:
@@ -168,6 +204,28 @@ class Instance:
         cur.update(kw)
         prm = Params(**cur)
         check(lib().usaphmp_set_params(self.h, ctypes.byref(prm)))
+
+    def set_tile(self, ntile, stages, raster):
+        """usaphmp_set_tile: tile shape of the tensor-core evaluator."""
+        t = Tile(ntile, stages, raster)
+        check(lib().usaphmp_set_tile(self.h, ctypes.byref(t)))
+
+    def get_tile(self):
+        t = Tile()
+        check(lib().usaphmp_get_tile(self.h, ctypes.byref(t)))
+        return _tile_dict(t)
+
+    def autotune(self, reps=20, cache=None):
+        """usaphmp_autotune: times the tile shapes, keeps the fastest.
+
+        Returns the chosen shape with "ms" (its mean launch time), "default_ms"
+        and "from_cache".  Resets the GA state (call ga_begin/solve after)."""
+        t, ms, dms, fc = Tile(), c_f64(), c_f64(), c_i32()
+        check(lib().usaphmp_autotune(self.h, reps, os.fsencode(cache) if cache else None, ctypes.byref(t),
+                                     ctypes.byref(ms), ctypes.byref(dms), ctypes.byref(fc)))
+        d = _tile_dict(t)
+        d.update(ms=ms.value, default_ms=dms.value, from_cache=bool(fc.value))
+        return d
 
     # public calls
     def eval(self, hubs, S):

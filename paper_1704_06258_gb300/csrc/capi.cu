@@ -89,6 +89,7 @@ struct usaphmp_s {
   __nv_bfloat16* Wlo = nullptr;
   void* tmaps = nullptr;  // two CUtensorMap in device memory
   usaphmp_params prm{};
+  TcTile tile{};  // tile shape of the tensor-core evaluator (usaphmp_set_tile / usaphmp_autotune)
   int num_sms = 0;
   cudaStream_t stream = nullptr;
   uint32_t* d_status = nullptr;
@@ -209,7 +210,7 @@ int reset_status(usaphmp_s* h, cudaStream_t s) {
 int run_transfer(usaphmp_s* h, const Task& task, cudaStream_t s) {
   TaskSet ts{nullptr, &task, 1};
   if (use_tc(h))
-    launch_eval_tc(ts, h->num_sms, h->d_status, s);
+    launch_eval_tc(ts, h->num_sms, h->d_status, s, h->tile);
   else
     launch_eval_plain(ts, s);
   CK(cudaGetLastError());
@@ -397,7 +398,7 @@ int enqueue_generation(usaphmp_s* h, cudaStream_t s) {
   launch_children(ts, s);
   launch_alloc(ts, true, use_tc(h), s);
   if (use_tc(h))
-    launch_eval_tc(ts, h->num_sms, h->d_status, s);
+    launch_eval_tc(ts, h->num_sms, h->d_status, s, h->tile);
   else
     launch_eval_plain(ts, s);
   launch_reduce_select(ts, s);
@@ -482,6 +483,109 @@ int usaphmp_set_params(usaphmp_t h, const usaphmp_params* prm) {
   h->ga_ready = false;
   drop_graph(h);
   return USAPHMP_OK;
+}
+
+int usaphmp_set_tile(usaphmp_t h, const usaphmp_tile* tile) {
+  if (!h || !tile) return fail(USAPHMP_EINVAL, "NULL argument");
+  TcTile t;
+  t.ntile = tile->ntile;
+  t.stages = tile->stages;
+  t.raster = tile->raster;
+  if (!tc_tile_fits(t, h->p))
+    return fail(USAPHMP_EINVAL, "tile shape: ntile in {64, 128, 256} and >= p, stages 2..4 within shared memory "
+                                "(ntile 256: at most 3), raster 0 or 1");
+  h->tile = t;
+  drop_graph(h);
+  return USAPHMP_OK;
+}
+
+int usaphmp_get_tile(usaphmp_t h, usaphmp_tile* tile) {
+  if (!h || !tile) return fail(USAPHMP_EINVAL, "NULL argument");
+  tile->ntile = h->tile.ntile;
+  tile->stages = h->tile.stages;
+  tile->raster = h->tile.raster;
+  return USAPHMP_OK;
+}
+
+int usaphmp_autotune(usaphmp_t h, int32_t reps, const char* cache_path, usaphmp_tile* chosen, double* chosen_ms,
+                     double* default_ms, int32_t* from_cache) {
+  if (!h) return fail(USAPHMP_EINVAL, "NULL handle");
+  if (reps < 1 || reps > 1000) return fail(USAPHMP_EINVAL, "reps must be in [1, 1000]");
+  if (from_cache) *from_cache = 0;
+  if (chosen_ms) *chosen_ms = 0;
+  if (default_ms) *default_ms = 0;
+  auto report = [&]() -> int {
+    if (chosen) RET(usaphmp_get_tile(h, chosen));
+    return USAPHMP_OK;
+  };
+  if (!use_tc(h)) return report();
+  const int B = h->prm.islands * h->prm.island_size;
+  int dev_id = 0;
+  CK(cudaGetDevice(&dev_id));
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, dev_id));
+  if (cache_path) {
+    usaphmp_tile t{};
+    const int r = usaphmp_tile_cache_lookup(cache_path, prop.name, h->n, h->p, B, &t, nullptr);
+    if (r < 0) return r;
+    if (r == 1 && usaphmp_set_tile(h, &t) == USAPHMP_OK) {
+      if (from_cache) *from_cache = 1;
+      return report();
+    }
+  }
+  // A population to time on: one generation grown from the initial solution.
+  cudaStream_t s = h->stream;
+  RET(usaphmp_ga_begin(h, 0x74756e65ull, s));
+  RET(enqueue_generation(h, s));
+  h->ga_ready = false;
+  std::vector<TcTile> cands{TcTile{}};
+  for (int nt : {256, 128, 64})
+    for (int st : {2, 3, 4})
+      for (int ra : {0, 1}) {
+        TcTile t;
+        t.ntile = nt; t.stages = st; t.raster = ra;
+        const TcTile d{};
+        const bool is_default = nt == d.ntile && st == d.stages && ra == d.raster;
+        if (!is_default && tc_tile_fits(t, h->p)) cands.push_back(t);
+      }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(ce, "cudaEventCreate"); }
+  TaskSet ts{nullptr, &h->ga_task, 1};
+  double best_ms = 0, dflt_ms = 0;
+  TcTile best{};
+  for (size_t k = 0; k < cands.size() && ce == cudaSuccess; ++k) {
+    launch_eval_tc(ts, h->num_sms, h->d_status, s, cands[k]);
+    ce = cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && ce == cudaSuccess; ++r) {
+      launch_eval_tc(ts, h->num_sms, h->d_status, s, cands[k]);
+      ce = cudaGetLastError();
+    }
+    if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+    if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+    const double per = (double)ms / reps;
+    if (k == 0) dflt_ms = per;
+    if (k == 0 || per < best_ms) {
+      best_ms = per;
+      best = cands[k];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(ce);
+  RET(check_status(h, s, "usaphmp_autotune"));
+  h->tile = best;
+  drop_graph(h);
+  if (cache_path) {
+    const usaphmp_tile t{best.ntile, best.stages, best.raster};
+    RET(usaphmp_tile_cache_store(cache_path, prop.name, h->n, h->p, B, &t, best_ms));
+  }
+  if (chosen_ms) *chosen_ms = best_ms;
+  if (default_ms) *default_ms = dflt_ms;
+  return report();
 }
 
 int usaphmp_get_params(usaphmp_t h, usaphmp_params* prm) {
@@ -685,7 +789,7 @@ int usaphmp_ga_run_profiled(usaphmp_t h, int32_t generations, void* stream, doub
     launch_alloc(ts, true, use_tc(h), s);
     CK(cudaEventRecord(h->prof_ev[2], s));
     if (use_tc(h))
-      launch_eval_tc(ts, h->num_sms, h->d_status, s);
+      launch_eval_tc(ts, h->num_sms, h->d_status, s, h->tile);
     else
       launch_eval_plain(ts, s);
     CK(cudaEventRecord(h->prof_ev[3], s));

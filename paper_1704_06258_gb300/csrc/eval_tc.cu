@@ -35,35 +35,53 @@ namespace usaphmp {
 
 namespace {
 
-constexpr int BM = 128, BNMAX = 256, BK = 64, STAGES = 3;
+constexpr int BM = 128, BK = 64;
 constexpr int kEpiWarp0 = 2, kEpiWarps = 8;
 constexpr int kProdWarp0 = kEpiWarp0 + kEpiWarps;
 constexpr int kThreads = 32 * (kProdWarp0 + 8);
 constexpr uint32_t A_BYTES = BM * BK * 2;                 // 16 KB
-constexpr uint32_t B_BYTES = BNMAX * BK * 2;              // 32 KB
-constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + B_BYTES;   // 64 KB
-constexpr uint32_t TMEM_COLS = 2 * BNMAX;
-constexpr uint32_t kSlabOffset = STAGES * STAGE_BYTES;    // Chub tables of the tile's chromosomes
-constexpr uint32_t kSlabBytes = 23552;
+constexpr int kMaxStages = 4;
 constexpr int kTblChrom = 86;                              // slot-code table: u8 [4 warps][86][32 rows]
-constexpr uint32_t kTblOffset = kSlabOffset + kSlabBytes;
 constexpr uint32_t kTblBytes = 4 * kTblChrom * 32;
-constexpr uint32_t kBarOffset = kTblOffset + kTblBytes;
-constexpr int kNumBars = 3 * STAGES + 7;
-constexpr size_t kSmemBytes = 1024 + kBarOffset + 8 * kNumBars + 8;
+constexpr int kNumBars = 3 * kMaxStages + 7;
+constexpr uint32_t kSmemBytes = 232448;                    // dynamic shared memory of one CTA (227 KB)
+constexpr uint32_t kUsable = kSmemBytes - 1024;            // after aligning the base to 1024
 constexpr uint64_t kTimeoutNs = 2000000000ull;
-static_assert(kSmemBytes <= 232448, "shared memory budget");
+
+// Shared-memory layout of a tile shape: `stages` stages of [A_hi | A_lo | B]
+// (B = ntile rows x 128 bytes), then the slab for the tile's Chub tables
+// (whatever room is left), the slot-code table and the barriers at the top.
+struct Lay {
+  int ntile, stages, raster;
+  uint32_t stage_bytes, slab_off, slab_bytes, tbl_off, bar_off;
+  bool ok;
+};
+
+__host__ __device__ inline Lay lay_of(const TcTile& t) {
+  Lay L;
+  L.ntile = t.ntile;
+  L.stages = t.stages;
+  L.raster = t.raster;
+  L.stage_bytes = 2 * A_BYTES + (uint32_t)t.ntile * BK * 2;
+  L.bar_off = (kUsable - (8 * kNumBars + 8)) & ~15u;
+  L.tbl_off = (L.bar_off - kTblBytes) & ~15u;
+  L.slab_off = (uint32_t)t.stages * L.stage_bytes;
+  L.ok = (t.ntile == 64 || t.ntile == 128 || t.ntile == 256) && t.stages >= 2 && t.stages <= kMaxStages &&
+         (t.raster == 0 || t.raster == 1) && L.slab_off <= L.tbl_off;
+  L.slab_bytes = L.ok ? (L.tbl_off - L.slab_off) & ~15u : 0;
+  return L;
+}
 
 struct Bars {
   uint32_t base;
   __device__ uint32_t full_tma(int s) const { return base + 8 * s; }
-  __device__ uint32_t full_oh(int s) const { return base + 8 * (STAGES + s); }
-  __device__ uint32_t empty(int s) const { return base + 8 * (2 * STAGES + s); }
-  __device__ uint32_t tfull(int b) const { return base + 8 * (3 * STAGES + b); }
-  __device__ uint32_t tempty(int b) const { return base + 8 * (3 * STAGES + 2 + b); }
-  __device__ uint32_t drain() const { return base + 8 * (3 * STAGES + 4); }
-  __device__ uint32_t slab_full() const { return base + 8 * (3 * STAGES + 5); }
-  __device__ uint32_t slab_empty() const { return base + 8 * (3 * STAGES + 6); }
+  __device__ uint32_t full_oh(int s) const { return base + 8 * (kMaxStages + s); }
+  __device__ uint32_t empty(int s) const { return base + 8 * (2 * kMaxStages + s); }
+  __device__ uint32_t tfull(int b) const { return base + 8 * (3 * kMaxStages + b); }
+  __device__ uint32_t tempty(int b) const { return base + 8 * (3 * kMaxStages + 2 + b); }
+  __device__ uint32_t drain() const { return base + 8 * (3 * kMaxStages + 4); }
+  __device__ uint32_t slab_full() const { return base + 8 * (3 * kMaxStages + 5); }
+  __device__ uint32_t slab_empty() const { return base + 8 * (3 * kMaxStages + 6); }
 };
 
 // Single-thread bounded wait.  Returns false on timeout or when another role
@@ -119,26 +137,50 @@ struct Geo {
   bool slab;  // Chub tables of a full tile fit in the shared slab
 };
 
-__host__ __device__ __forceinline__ Geo geo_of(int p, int B) {
+__host__ __device__ __forceinline__ Geo geo_of(int p, int B, const Lay& L) {
   Geo g;
-  g.cpt = BNMAX / p;
+  g.cpt = L.ntile / p;
   g.nt = (B + g.cpt - 1) / g.cpt;
-  g.slab = (size_t)g.cpt * chub_cstride(p) * 4 <= kSlabBytes;
+  g.slab = (size_t)g.cpt * chub_cstride(p) * 4 <= L.slab_bytes;
   return g;
 }
+
+// Position in the ring of shared-memory stages: stage index and the parity
+// of its current use, advanced without a division per K block.
+struct Ring {
+  int s = 0, n;
+  uint32_t ph = 0;
+  __device__ explicit Ring(int stages) : n(stages) {}
+  __device__ void next() {
+    if (++s == n) {
+      s = 0;
+      ph ^= 1u;
+    }
+  }
+};
 
 struct TileRef {
   int task, m, nb;
 };
 
-__device__ __forceinline__ TileRef decode_tile(const TaskParam& tp, int g) {
+// Tile g of the launch -> (task, row block m, column tile nb).  Raster 0
+// walks the column tiles of one row block first (CTAs running side by side
+// share the W stripe), raster 1 the row blocks of one column tile first
+// (they share the chromosomes' slot codes and hub tables).
+__device__ __forceinline__ TileRef decode_tile(const TaskParam& tp, int g, const Lay& L) {
   TileRef r;
   r.task = task_of(tp.bo, g);
   const Task& T = task_at(tp, r.task);
   const int local = g - tp.bo.o[r.task];
-  const int nt = geo_of(T.in.p, T.pop.B).nt;
-  r.m = local / nt;
-  r.nb = local - r.m * nt;
+  if (L.raster == 0) {
+    const int nt = geo_of(T.in.p, T.pop.B, L).nt;
+    r.m = local / nt;
+    r.nb = local - r.m * nt;
+  } else {
+    const int mt = (T.in.n + BM - 1) / BM;
+    r.nb = local / mt;
+    r.m = local - r.nb * mt;
+  }
   return r;
 }
 
@@ -261,18 +303,21 @@ __device__ __forceinline__ void epi_chromosomes(const EpiArgs& a) {
 }  // namespace
 
 __global__ void __launch_bounds__(kThreads, 1)
-    k_eval_tc(const __grid_constant__ TaskParam tp, int total_tiles, uint32_t* status) {
+    k_eval_tc(const __grid_constant__ TaskParam tp, int total_tiles, uint32_t* status, const Lay L) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uint32_t raw = ptx::smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   unsigned char* sm = smem_raw + (base - raw);
-  const Bars bars{base + kBarOffset};
-  volatile uint32_t* tmem_holder = reinterpret_cast<volatile uint32_t*>(sm + kBarOffset + 8 * kNumBars);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + kBarOffset + 8 * kNumBars + 4);
+  const Bars bars{base + L.bar_off};
+  volatile uint32_t* tmem_holder = reinterpret_cast<volatile uint32_t*>(sm + L.bar_off + 8 * kNumBars);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + L.bar_off + 8 * kNumBars + 4);
+  const int STAGES = L.stages;
+  const uint32_t STAGE_BYTES = L.stage_bytes;
+  const uint32_t tmem_cols = 2u * (uint32_t)L.ntile;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < kMaxStages; ++s) {
       ptx::mbar_init(bars.full_tma(s), 1);
       ptx::mbar_init(bars.full_oh(s), 256);
       ptx::mbar_init(bars.empty(s), 1);
@@ -288,7 +333,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     ptx::fence_mbar_init();
   }
   if (warp == 1) {
-    ptx::tmem_alloc(ptx::smem_u32(const_cast<uint32_t*>(tmem_holder)), TMEM_COLS);
+    ptx::tmem_alloc(ptx::smem_u32(const_cast<uint32_t*>(tmem_holder)), tmem_cols);
     ptx::tmem_relinquish();
   }
   ptx::tc_fence_before();
@@ -299,15 +344,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------------------ TMA producer
     int it = 0;
+    Ring ring(STAGES);
     bool ok = true;
     for (int g = blockIdx.x; g < total_tiles && ok; g += gridDim.x) {
-      const TileRef tr = decode_tile(tp, g);
+      const TileRef tr = decode_tile(tp, g, L);
       const Task& T = task_at(tp, tr.task);
       const int nk = (T.in.n + BK - 1) / BK;
-      for (int kb = 0; kb < nk; ++kb, ++it) {
-        const int s = it % STAGES;
-        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-        if (!(ok = wait_one(bars.empty(s), ph ^ 1u, abort_flag, status))) break;
+      for (int kb = 0; kb < nk; ++kb, ++it, ring.next()) {
+        const int s = ring.s;
+        if (!(ok = wait_one(bars.empty(s), ring.ph ^ 1u, abort_flag, status))) break;
         const uint32_t a_hi = base + s * STAGE_BYTES;
         ptx::mbar_arrive_expect_tx(bars.full_tma(s), 2 * A_BYTES);
         ptx::tma_load_2d(a_hi, T.tmap_hi, kb * BK, tr.m * BM, bars.full_tma(s));
@@ -318,13 +363,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       wait_drain(bars.full_tma(j % STAGES), (uint32_t)(j / STAGES) & 1u);
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------------------- MMA issuer
-    int it = 0, tl = 0;
+    int tl = 0;
+    Ring ring(STAGES);
     bool ok = true;
     for (int g = blockIdx.x; g < total_tiles && ok; g += gridDim.x, ++tl) {
-      const TileRef tr = decode_tile(tp, g);
+      const TileRef tr = decode_tile(tp, g, L);
       const Task& T = task_at(tp, tr.task);
       const int p = T.in.p;
-      const Geo geo = geo_of(p, T.pop.B);
+      const Geo geo = geo_of(p, T.pop.B, L);
       const int nchrom = min(geo.cpt, T.pop.B - tr.nb * geo.cpt);
       const uint32_t idesc = ptx::idesc_bf16_f32(BM, round_up(nchrom * p, 16));
       const int nk = (T.in.n + BK - 1) / BK;
@@ -332,12 +378,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t use = (uint32_t)(tl >> 1);
       if (!(ok = wait_one(bars.tempty(buf), (use & 1u) ^ 1u, abort_flag, status))) break;
       ptx::tc_fence_after();
-      const uint32_t d = tmem + (uint32_t)(buf * BNMAX);
-      for (int kb = 0; kb < nk; ++kb, ++it) {
-        const int s = it % STAGES;
-        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-        if (!(ok = wait_one(bars.full_tma(s), ph, abort_flag, status))) break;
-        if (!(ok = wait_one(bars.full_oh(s), ph, abort_flag, status))) break;
+      const uint32_t d = tmem + (uint32_t)(buf * L.ntile);
+      for (int kb = 0; kb < nk; ++kb, ring.next()) {
+        const int s = ring.s;
+        if (!(ok = wait_one(bars.full_tma(s), ring.ph, abort_flag, status))) break;
+        if (!(ok = wait_one(bars.full_oh(s), ring.ph, abort_flag, status))) break;
         ptx::tc_fence_after();
         const uint32_t a_hi = base + s * STAGE_BYTES, a_lo = a_hi + A_BYTES, bt = a_lo + A_BYTES;
 #pragma unroll
@@ -355,14 +400,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + kEpiWarps) {
     // --------------------------------------------------------------- epilogue
     const int quarter = warp & 3, half = (warp - kEpiWarp0) >> 2;
-    uint8_t* tbl = sm + kTblOffset + quarter * (kTblChrom * 32);
-    const float* slab = reinterpret_cast<const float*>(sm + kSlabOffset);
+    uint8_t* tbl = sm + L.tbl_off + quarter * (kTblChrom * 32);
+    const float* slab = reinterpret_cast<const float*>(sm + L.slab_off);
     int tl = 0;
     for (int g = blockIdx.x; g < total_tiles; g += gridDim.x, ++tl) {
-      const TileRef tr = decode_tile(tp, g);
+      const TileRef tr = decode_tile(tp, g, L);
       const Task& T = task_at(tp, tr.task);
       const int n = T.in.n, p = T.in.p, ns = T.in.ns, B = T.pop.B;
-      const Geo geo = geo_of(p, B);
+      const Geo geo = geo_of(p, B, L);
       const int b0 = tr.nb * geo.cpt;
       const int nchrom = min(geo.cpt, B - b0);
       const int hst = chub_hstride(p), cst = chub_cstride(p);
@@ -381,7 +426,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (geo.slab) {
             const uint32_t bytes = (uint32_t)(nchrom * cst * 4);
             ptx::mbar_arrive_expect_tx(bars.slab_full(), bytes);
-            ptx::bulk_load(base + kSlabOffset, chub, bytes, bars.slab_full());
+            ptx::bulk_load(base + L.slab_off, chub, bytes, bars.slab_full());
           } else {
             ptx::mbar_arrive(bars.slab_full());
           }
@@ -406,7 +451,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!wait_warp(bars.tfull(buf), use & 1u, abort_flag, status)) break;
       if (!wait_warp(bars.slab_full(), (uint32_t)(tl & 1), abort_flag, status)) break;
       ptx::tc_fence_after();
-      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BNMAX);
+      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * L.ntile);
       float* __restrict__ out = T.pop.part + (long long)(tr.m * 4 + quarter) * B + b0;
       const float* fbase = geo.slab ? slab : chub;
       // one code path per TMEM load width (the widest that keeps every
@@ -427,13 +472,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp >= kProdWarp0) {
     // -------------------------------------------------------- one-hot producers
     const int r = threadIdx.x - 32 * kProdWarp0;
-    int it = 0;
+    Ring ring(STAGES);
     bool ok = true;
     for (int g = blockIdx.x; g < total_tiles && ok; g += gridDim.x) {
-      const TileRef tr = decode_tile(tp, g);
+      const TileRef tr = decode_tile(tp, g, L);
       const Task& T = task_at(tp, tr.task);
       const int n = T.in.n, p = T.in.p, ns = T.in.ns, B = T.pop.B;
-      const Geo geo = geo_of(p, B);
+      const Geo geo = geo_of(p, B, L);
       const int b0 = tr.nb * geo.cpt;
       const int nchrom = min(geo.cpt, B - b0);
       const int nmma = round_up(nchrom * p, 16);
@@ -450,15 +495,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       // slot codes of the next K block are loaded one block ahead
       uint4 n0 = zero4, n1 = zero4, n2 = zero4, n3 = zero4;
       if (valid) { n0 = __ldg(src); n1 = __ldg(src + 1); n2 = __ldg(src + 2); n3 = __ldg(src + 3); }
-      for (int kb = 0; kb < nk; ++kb, ++it) {
+      for (int kb = 0; kb < nk; ++kb, ring.next()) {
         const uint4 q0 = n0, q1 = n1, q2 = n2, q3 = n3;
         if (valid && kb + 1 < nk) {
           const uint4* nx = src + (kb + 1) * (BK / 16);
           n0 = __ldg(nx); n1 = __ldg(nx + 1); n2 = __ldg(nx + 2); n3 = __ldg(nx + 3);
         }
-        const int s = it % STAGES;
-        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-        if (!(ok = wait_warp(bars.empty(s), ph ^ 1u, abort_flag, status))) break;
+        const int s = ring.s;
+        if (!(ok = wait_warp(bars.empty(s), ring.ph ^ 1u, abort_flag, status))) break;
         const uint32_t dst = base + s * STAGE_BYTES + 2 * A_BYTES + (uint32_t)r * 128u;
         if (valid && small) {
           st_shared_v4(dst + ((0u ^ swz) << 4), onehot8_small(q0.x, q0.y, lrep));
@@ -492,7 +536,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   if (warp == 1) {
     ptx::tc_fence_after();
-    ptx::tmem_dealloc(tmem, TMEM_COLS);
+    ptx::tmem_dealloc(tmem, tmem_cols);
   }
 }
 
@@ -502,17 +546,26 @@ void prepare_eval_tc() {
   cudaFuncSetAttribute(k_eval_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
 }
 
-void launch_eval_tc(const TaskSet& ts, int num_sms, uint32_t* status, cudaStream_t s) {
+bool tc_tile_fits(const TcTile& t, int p) { return lay_of(t).ok && p <= t.ntile; }
+
+size_t tc_slab_bytes(const TcTile& t) { return lay_of(t).slab_bytes; }
+
+void launch_eval_tc(const TaskSet& ts, int num_sms, uint32_t* status, cudaStream_t s, const TcTile& tile) {
+  // a shape that does not fit every task of the launch falls back to the default
+  TcTile t = tile;
+  for (int k = 0; k < ts.count; ++k)
+    if (!tc_tile_fits(t, ts.h[k].in.p)) t = TcTile{};
+  const Lay L = lay_of(t);
   TaskParam tp = make_param(ts);
-  for (int t = 0; t < ts.count; ++t) {
-    const Task& T = ts.h[t];
+  for (int k = 0; k < ts.count; ++k) {
+    const Task& T = ts.h[k];
     const int mt = (T.in.n + BM - 1) / BM;
-    tp.bo.o[t + 1] = tp.bo.o[t] + (T.pop.B > 0 ? mt * geo_of(T.in.p, T.pop.B).nt : 0);
+    tp.bo.o[k + 1] = tp.bo.o[k] + (T.pop.B > 0 ? mt * geo_of(T.in.p, T.pop.B, L).nt : 0);
   }
   const int total = tp.bo.o[ts.count];
   if (total == 0) return;
   const int grid = total < num_sms ? total : num_sms;
-  k_eval_tc<<<grid, kThreads, kSmemBytes, s>>>(tp, total, status);
+  k_eval_tc<<<grid, kThreads, kSmemBytes, s>>>(tp, total, status, L);
 }
 
 }  // namespace usaphmp

@@ -78,7 +78,21 @@ void prepare_eval_plain(int max_smem);
 
 // eval_tc.cu: split-bf16 tcgen05 transfer sums into pop.part[r][b] with r
 // the 32-row group of W (tc_part_rows(n) = 4*ceil(n/128) rows).
-void launch_eval_tc(const TaskSet& ts, int num_sms, uint32_t* status, cudaStream_t s);
+// Tile shape of a launch: MMA width ntile (64, 128 or 256 columns; a tile
+// holds floor(ntile/p) chromosomes), shared-memory stages (2..4) and the
+// raster order of the persistent tile loop (0: column tiles of a row block
+// first, 1: row blocks of a column tile first).  The results do not depend
+// on it.
+struct TcTile {
+  int ntile = 256;
+  int stages = 3;
+  int raster = 0;
+};
+// true when the shape's layout fits shared memory and p <= ntile
+bool tc_tile_fits(const TcTile& t, int p);
+size_t tc_slab_bytes(const TcTile& t);
+void launch_eval_tc(const TaskSet& ts, int num_sms, uint32_t* status, cudaStream_t s,
+                    const TcTile& tile = TcTile{});
 int tc_part_rows(int n);
 void prepare_eval_tc();
 
