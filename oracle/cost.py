@@ -6,9 +6,15 @@ Definitions follow the paper:
   the cost of routing W[i, j] from i to j is collection at rate chi on arc
   (i, h(i)), transfer at discount alpha on the hub arc (h(i), h(j)) and
   distribution at rate delta on (h(j), j) -- the path cost written out in
-  §6.2.  Eq. (4) lets hub-to-hub flow take any path between hubs; with C
-  satisfying the triangle inequality (every instance generated here is
-  Euclidean) the direct hub arc is a shortest path, so the direct arc is used.
+  §6.2.  Eq. (4) lets hub-to-hub flow take any path; with C satisfying the
+  triangle inequality (every Euclidean instance) the direct hub arc is a
+  shortest path, which is `routing="direct"`.  For C without it (§6.1's
+  PlanetLab latencies) the transfer leg takes a shortest path:
+  `routing="hubs"` over arcs between open hubs only (§3 defines Y^i_kl as
+  flow between hubs k and l), `routing="all"` over arcs between any nodes (what
+  constraints (4) alone admit: a non-hub node is a zero-balance transshipment
+  node there).  Both give a same-hub pair a zero transfer leg (flow from k to
+  k needs no Y in eq. 4).
 * O_i and D_j are the originating and destined flows of §3 (row and column
   sums of W).
 * Middle nodes, §4.1: the p nodes with the smallest d_i = sum_j C[i, j]
@@ -60,29 +66,66 @@ def check_allocation(n, hubs, h):
             raise ValueError(f"hub {k} not allocated to itself")
 
 
-def pair_cost(W, C, chi, alpha, delta, h):
+def floyd_warshall(A):
+    """Shortest-path costs over a complete digraph with arc costs A (FP64).
+
+    The textbook recurrence: after step k, D[a, b] is the cheapest path from a
+    to b whose intermediate vertices are among the first k + 1; D[a, a] = 0.
+    """
+    D = _f64(A).copy()
+    np.fill_diagonal(D, 0.0)
+    for k in range(D.shape[0]):
+        D = np.minimum(D, D[:, k:k + 1] + D[k:k + 1, :])
+    return D
+
+
+def transfer_costs(C, h, routing="direct"):
+    """n x n matrix T with T[a, b] the unit cost of the transfer leg from hub a
+    to hub b (entries between non-hubs are unused).
+
+    direct: C itself; hubs: shortest paths over arcs between the open hubs
+    (the distinct values of h); all: shortest paths over arcs between any
+    nodes.
+    """
+    C = _f64(C)
+    if routing == "direct":
+        return C
+    if routing == "all":
+        return floyd_warshall(C)
+    if routing != "hubs":
+        raise ValueError(routing)
+    hubs = np.unique(np.asarray(h, dtype=np.int64))
+    T = C.copy()
+    T[np.ix_(hubs, hubs)] = floyd_warshall(C[np.ix_(hubs, hubs)])
+    return T
+
+
+def pair_cost(W, C, chi, alpha, delta, h, routing="direct"):
     """Objective (1) summed pair by pair in FP64.
 
-    cost = sum_i sum_j W[i,j] * (chi*C[i,h(i)] + alpha*C[h(i),h(j)] + delta*C[h(j),j])
+    cost = sum_i sum_j W[i,j] * (chi*C[i,h(i)] + alpha*T[h(i),h(j)] + delta*C[h(j),j])
+    with T the transfer-leg costs of `routing` (T = C for the direct arc).
     """
     W = _f64(W)
     C = _f64(C)
     h = np.asarray(h, dtype=np.int64)
     n = W.shape[0]
     idx = np.arange(n)
+    T = transfer_costs(C, h, routing)
     collect = C[idx, h]                  # C[i, h(i)]
-    transfer = C[h[:, None], h[None, :]]  # C[h(i), h(j)]
+    transfer = T[h[:, None], h[None, :]]  # T[h(i), h(j)]
     distribute = C[h, idx]               # C[h(j), j]
     per_pair = W * (chi * collect[:, None] + alpha * transfer + delta * distribute[None, :])
     return math.fsum(np.sum(per_pair, axis=1))
 
 
-def three_term_cost(W, C, chi, alpha, delta, hubs, h):
+def three_term_cost(W, C, chi, alpha, delta, hubs, h, routing="direct"):
     """The same objective regrouped as the GPU evaluates it.
 
     chi * sum_i O_i C[i,h(i)] + delta * sum_j D_j C[h(j),j]
-      + alpha * sum_i sum_l M[i,l] C[h(i), hubs[l]],   M = W A,
-    with A the n x p one-hot matrix A[j, l] = [h(j) == hubs[l]].
+      + alpha * sum_i sum_l M[i,l] T[h(i), hubs[l]],   M = W A,
+    with A the n x p one-hot matrix A[j, l] = [h(j) == hubs[l]] and T the
+    transfer-leg costs of `routing`.
     Returns (total, collect_term, distribute_term, transfer_term).
     """
     W = _f64(W)
@@ -99,7 +142,8 @@ def three_term_cost(W, C, chi, alpha, delta, hubs, h):
     for l in range(p):
         A[h == hubs[l], l] = 1.0
     M = W @ A
-    t_transfer = alpha * math.fsum(np.sum(M * C[h[:, None], hubs[None, :]], axis=1))
+    T = transfer_costs(C, hubs, routing)
+    t_transfer = alpha * math.fsum(np.sum(M * T[h[:, None], hubs[None, :]], axis=1))
     return t_collect + t_distribute + t_transfer, t_collect, t_distribute, t_transfer
 
 

@@ -154,13 +154,15 @@ def select(state, children, fitness, g, P, N1, elitist=False):
     return state
 
 
-def solve(inst, generations, seed, R=1, P=64, N1=10, elitist=False, fitness_fn=None):
-    """The whole GA on one instance with FP64 fitness; returns (hubs, h, cost, state)."""
+def solve(inst, generations, seed, R=1, P=64, N1=10, elitist=False, fitness_fn=None, routing="direct"):
+    """The whole GA on one instance with FP64 fitness; returns (hubs, h, cost, state).
+
+    `routing` is the transfer leg of the objective (cost.transfer_costs)."""
     W, C = inst.W, inst.C
     n, p = inst.n, inst.p
     if fitness_fn is None:
         def fitness_fn(h):
-            return _cost.pair_cost(W, C, inst.chi, inst.alpha, inst.delta, h)
+            return _cost.pair_cost(W, C, inst.chi, inst.alpha, inst.delta, h, routing)
     hubs0, h0 = _cost.initial_solution(C, p)
     mask0 = np.zeros(n, dtype=bool)
     mask0[hubs0] = True
@@ -173,4 +175,4 @@ def solve(inst, generations, seed, R=1, P=64, N1=10, elitist=False, fitness_fn=N
         select(state, children, fit, g, P, N1, elitist)
     hubs = np.flatnonzero(state.best)
     h = _cost.nearest_allocation(C, hubs)
-    return hubs, h, _cost.pair_cost(W, C, inst.chi, inst.alpha, inst.delta, h), state
+    return hubs, h, _cost.pair_cost(W, C, inst.chi, inst.alpha, inst.delta, h, routing), state

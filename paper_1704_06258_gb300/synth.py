@@ -94,6 +94,24 @@ def large_uniform(seed: int = 1004, n: int = 6000, p: int = 20) -> Instance:
     return Instance(f"uniform_n{n}_p{p}", n, p, _zero_diag(W), _euclid_fp32(xy), xy=xy)
 
 
+def latency_like(seed: int = 1005, n: int = 200, p: int = 10, spread: float = 0.6) -> Instance:
+    """Non-metric costs standing in for the PlanetLab latencies of §6.1:
+    coordinates uniform in [0,1000]^2, each Euclidean distance multiplied by
+    a lognormal(0, spread) factor drawn once per unordered pair (so C stays
+    symmetric with a zero diagonal but violates the triangle inequality on
+    many triples); W lognormal(0, 1)."""
+    rng = _rng(seed)
+    xy = uniform_points(rng, n, 1000.0)
+    d = xy[:, None, :] - xy[None, :, :]
+    E = np.sqrt(d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1])
+    f = rng.lognormal(0.0, spread, size=(n, n))
+    f = np.triu(f, 1)
+    f = f + f.T
+    C = (E * f).astype(np.float32)
+    W = _zero_diag(rng.lognormal(0.0, 1.0, size=(n, n)).astype(np.float32))
+    return Instance(f"latency_n{n}_p{p}", n, p, W, _zero_diag(C), xy=xy)
+
+
 def serving_request(r: int):
     """Request r of the serving mix: n log-uniform in [50, 3000], p in 3..20,
     instance drawn like the clustered family from seed 5000 + r."""

@@ -64,12 +64,15 @@ def test_hand4_brute_force(golden_dir):
     np.testing.assert_array_equal(res["nearest"][1], _ints(near[3]))
 
 
-def _mip_optimum(W, C, chi, alpha, delta, p):
+def _mip_optimum(W, C, chi, alpha, delta, p, hub_arcs_only=False):
     """Optimum of the MIP (1)-(5) of §3 (Ernst-Krishnamoorthy form), by HiGHS.
 
     Variables Z[i,k] (binary) then Y[i,k,l] >= 0 (flow from origin i on hub arc k->l).
     Eq. (1) as printed charges C[i,k] (chi O_i + delta D_i); the instances used
     here have symmetric C, where that equals the oracle's delta D_j C[h(j), j].
+    With hub_arcs_only, Y[i,k,l] <= O_i Z[k,k] and Y[i,k,l] <= O_i Z[l,l] keep
+    the flow on arcs between open hubs (§3 defines Y as flow between hubs);
+    without it constraints (4) also let flow pass through non-hub nodes.
     """
     W = np.asarray(W, np.float64)
     C = np.asarray(C, np.float64)
@@ -108,6 +111,19 @@ def _mip_optimum(W, C, chi, alpha, delta, p):
     for k in range(n):                      # (5)
         A[row, zi(k, k)] = 1
     lb.append(p); ub.append(p)
+    if hub_arcs_only:
+        extra = sp.lil_matrix((2 * ny, nz + ny))
+        r = 0
+        for i in range(n):
+            for k in range(n):
+                for l in range(n):
+                    for end in (k, l):
+                        extra[r, yi(i, k, l)] = 1
+                        extra[r, zi(end, end)] = -O[i]
+                        r += 1
+        A = sp.vstack([A.tocsr(), extra.tocsr()]).tolil()
+        lb += [-np.inf] * (2 * ny)
+        ub += [0.0] * (2 * ny)
     integrality = np.concatenate([np.ones(nz), np.zeros(ny)])
     bounds = so.Bounds(np.zeros(nz + ny), np.concatenate([np.ones(nz), np.full(ny, np.inf)]))
     res = so.milp(c, integrality=integrality, bounds=bounds,
@@ -195,3 +211,95 @@ def test_fig1_encoding(golden_dir):
     with pytest.raises(ValueError):
         bad = S.copy(); bad[0] = 0     # node allocated to a spoke
         cost.check_allocation(n, hubs, bad)
+
+
+def _hand4_nonmetric(golden_dir):
+    rows = [ln.split() for ln in open(os.path.join(golden_dir, "hand4_nonmetric.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    x = np.array([float(v) for v in next(r for r in rows if r[0] == "x")[1:]])
+    W = np.array([[float(v) for v in r[1:]] for r in rows if r[0] == "W"], dtype=np.float32)
+    chi, alpha, delta = (float(v) for v in next(r for r in rows if r[0] == "params")[1:])
+    C = np.abs(x[:, None] - x[None, :])
+    for r in rows:
+        if r[0] == "override":
+            a, b, v = int(r[1]), int(r[2]), float(r[3])
+            C[a, b] = C[b, a] = v
+    return rows, W, C.astype(np.float32), chi, alpha, delta
+
+
+def test_hand4_nonmetric_costs_by_routing(golden_dir):
+    rows, W, C, chi, alpha, delta = _hand4_nonmetric(golden_dir)
+    seen = set()
+    for r in rows:
+        if r[0] != "cost":
+            continue
+        routing, hubs, h, val = r[1], _ints(r[2]), _ints(r[3]), float(r[4])
+        cost.check_allocation(4, hubs, h)
+        assert cost.pair_cost(W, C, chi, alpha, delta, h, routing) == pytest.approx(val, rel=1e-15)
+        assert cost.three_term_cost(W, C, chi, alpha, delta, hubs, h, routing)[0] == pytest.approx(val, rel=1e-15)
+        seen.add(routing)
+    assert seen == {"direct", "hubs", "all"}
+
+
+def _enumerated_paths(A):
+    """Cheapest path cost between every ordered pair by trying every sequence
+    of distinct intermediate vertices (exponential; tiny sizes only)."""
+    import itertools
+    m = A.shape[0]
+    best = np.full((m, m), np.inf)
+    for a in range(m):
+        best[a, a] = 0.0
+        for b in range(m):
+            if a == b:
+                continue
+            rest = [v for v in range(m) if v not in (a, b)]
+            for r in range(len(rest) + 1):
+                for mid in itertools.permutations(rest, r):
+                    path = (a,) + mid + (b,)
+                    best[a, b] = min(best[a, b], sum(A[u, v] for u, v in zip(path, path[1:])))
+    return best
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_floyd_warshall_equals_path_enumeration(seed):
+    rng = np.random.default_rng(seed)
+    A = rng.lognormal(0.0, 1.2, size=(6, 6))
+    np.testing.assert_allclose(cost.floyd_warshall(A), _enumerated_paths(A), rtol=1e-14)
+    assert (cost.floyd_warshall(A) <= np.where(np.eye(6, dtype=bool), 0.0, A) + 1e-12).all()
+
+
+def _nonmetric_cases(golden_dir):
+    _, W, C, chi, alpha, delta = _hand4_nonmetric(golden_dir)
+    cases = [(W, C, chi, alpha, delta, p) for p in (1, 2, 3)]
+    for seed, n, p in ((31, 6, 2), (32, 7, 3)):
+        inst = synth.latency_like(seed=seed, n=n, p=p, spread=1.0)
+        cases.append((inst.W, inst.C, inst.chi, inst.alpha, inst.delta, p))
+    return cases
+
+
+def test_hub_routing_matches_mip_restricted_to_hub_arcs(golden_dir):
+    for W, C, chi, alpha, delta, p in _nonmetric_cases(golden_dir):
+        bf = brute.brute_force(W, C, chi, alpha, delta, p, routing="hubs")
+        mip = _mip_optimum(W, C, chi, alpha, delta, p, hub_arcs_only=True)
+        assert mip == pytest.approx(bf["opt"][0], rel=1e-9)
+        assert bf["opt"][0] <= brute.brute_force(W, C, chi, alpha, delta, p)["opt"][0]
+
+
+def test_all_node_routing_matches_mip_as_printed(golden_dir):
+    for W, C, chi, alpha, delta, p in _nonmetric_cases(golden_dir):
+        bf = brute.brute_force(W, C, chi, alpha, delta, p, routing="all")
+        assert _mip_optimum(W, C, chi, alpha, delta, p) == pytest.approx(bf["opt"][0], rel=1e-9)
+
+
+def test_routing_changes_nothing_on_euclidean_instances():
+    inst = synth.urand200(seed=41, n=60, p=6)
+    hubs, S = synth.random_population(42, inst.n, inst.p, 5)
+    for s in S:
+        direct = cost.pair_cost(inst.W, inst.C, inst.chi, inst.alpha, inst.delta, s)
+        for routing in ("hubs", "all"):
+            assert cost.pair_cost(inst.W, inst.C, inst.chi, inst.alpha, inst.delta, s, routing) == \
+                pytest.approx(direct, rel=1e-6)
+    tiny = synth.tiny(seed=43, n=7, p=3)
+    opts = [brute.brute_force(tiny.W, tiny.C, tiny.chi, tiny.alpha, tiny.delta, 3, r)["opt"][0]
+            for r in ("direct", "hubs", "all")]
+    assert opts[1] == pytest.approx(opts[0], rel=1e-6) and opts[2] == pytest.approx(opts[0], rel=1e-6)
