@@ -47,6 +47,19 @@ enum {
   USAPHMP_EIO = -7            /* a file could not be written */
 };
 
+/* Transfer leg of objective (1) between the hubs h(i) and h(j) (eq. 4 lets
+ * flow take any path between hubs).  DIRECT: the arc C[h(i)][h(j)], a
+ * shortest path whenever C satisfies the triangle inequality.  HUB_PATHS:
+ * the cheapest path over arcs between the chromosome's open hubs
+ * (Floyd-Warshall on its p x p hub costs, §3 defines Y^i_kl as flow between
+ * hubs k and l); a pair served by one hub has no transfer leg.  For C with a
+ * zero diagonal and the triangle inequality both give the same cost up to
+ * rounding. */
+enum {
+  USAPHMP_ROUTE_DIRECT = 0,
+  USAPHMP_ROUTE_HUB_PATHS = 1
+};
+
 /* Evaluators of the transfer term. */
 enum {
   USAPHMP_PATH_PLAIN_FP32 = 0,  /* fp32 CUDA cores, shared-memory gather of C[h(i)][h(j)] */
@@ -64,6 +77,10 @@ typedef struct {
   int32_t path;         /* USAPHMP_PATH_* (default SPLIT_BF16) */
   int32_t elitist;      /* 0 (default): ancestor = best child unconditionally */
   int32_t use_graph;    /* 1 (default): replay generations from a CUDA graph */
+  int32_t routing;      /* USAPHMP_ROUTE_* (default DIRECT); applies to every
+                           evaluation, generation and fp64 rescoring of the
+                           handle (the server and the allocation-free entry
+                           point use DIRECT) */
 } usaphmp_params;
 
 typedef struct {

@@ -4,7 +4,10 @@
 //               serves itself),
 //   t12_b     = sum_i chi*O_i*C[i,h(i)] + delta*D_i*C[h(i),i],
 // plus, for the tensor-core evaluator, the hub-to-hub cost table
-// chub_b[k][l] = C[hubs_b[k], hubs_b[l]] (layout in common.cuh).
+// chub_b[k][l] = C[hubs_b[k], hubs_b[l]] (layout in common.cuh).  With
+// hub-path routing (eq. 4) the table holds instead the cheapest path cost
+// over arcs between the chromosome's open hubs, zero on the diagonal
+// (Floyd-Warshall in place, one pass per intermediate hub).
 // One block per chromosome; C[i, hub] is read as CT[hub][i], so the p loads
 // of each node are coalesced across the block.
 #include "common.cuh"
@@ -78,12 +81,27 @@ __global__ void __launch_bounds__(256) k_alloc(const __grid_constant__ TaskParam
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(T.pop.status, kStatusBadChromosome);
   const float s = block_sum(acc, red);
   if (threadIdx.x == 0) T.pop.t12[b] = s;
-  if (with_chub || plain_global_table(p, T.in.ns)) {
+  const bool routed = T.in.routing != 0;
+  if (with_chub || routed || plain_global_table(p, T.in.ns)) {
     const int hst = chub_hstride(p), cst = chub_cstride(p);
-    float* __restrict__ ch = T.pop.chub + (long long)b * cst;
+    float* ch = T.pop.chub + (long long)b * cst;
     for (int e = threadIdx.x; e < cst; e += blockDim.x) {
       const int k = e / hst, l = e - k * hst;
-      ch[e] = (k < p && l < p) ? C[(long long)hs[k] * ldw + hs[l]] : 0.f;
+      ch[e] = (k < p && l < p && !(routed && k == l)) ? C[(long long)hs[k] * ldw + hs[l]] : 0.f;
+    }
+    if (routed) {
+      // Pass m relaxes every (a, c) through hub m.  Row m and column m do not
+      // change during pass m (their diagonal entry is 0 and costs are >= 0),
+      // so the in-place updates of one pass do not race.
+      __syncthreads();
+      for (int m = 0; m < p; ++m) {
+        for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+          const int a = e / p, c = e - a * p;
+          const float v = ch[a * hst + m] + ch[m * hst + c];
+          if (v < ch[a * hst + c]) ch[a * hst + c] = v;
+        }
+        __syncthreads();
+      }
     }
   }
 }

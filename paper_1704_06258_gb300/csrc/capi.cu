@@ -100,6 +100,7 @@ struct usaphmp_s {
   double* d_cost = nullptr;
   double* d_rpart = nullptr;
   int rpart_cap = 0;
+  double* d_dist64 = nullptr;  // p*p fp64 hub-path table of the returned solution (hub-path routing)
   // evaluation workspace and host-call staging
   Pop ev;
   int32_t* d_hubs_in = nullptr;
@@ -132,6 +133,7 @@ DevInst inst_of(const usaphmp_s* h) {
   DevInst in;
   in.n = h->n; in.p = h->p; in.ldw = h->ldw; in.ns = h->ns; in.nw = h->nw;
   in.symmetric = h->symmetric;
+  in.routing = h->prm.routing;
   in.chi = (float)h->chi; in.alpha = (float)h->alpha; in.delta = (float)h->delta;
   in.W = h->W; in.C = h->C; in.CT = h->symmetric ? h->C : h->CTbuf;
   in.O = h->O; in.D = h->D; in.Whi = h->Whi; in.Wlo = h->Wlo;
@@ -323,6 +325,7 @@ int create_impl(int32_t n, int32_t p, const float* W, const float* C, double chi
   h->prm.path = USAPHMP_PATH_SPLIT_BF16;
   h->prm.elitist = 0;
   h->prm.use_graph = 1;
+  h->prm.routing = USAPHMP_ROUTE_DIRECT;
   const int r = create_common(h, W, C, dev, static_cast<cudaStream_t>(stream));
   if (r != USAPHMP_OK) {
     const std::string msg = g_err;
@@ -379,6 +382,7 @@ int ensure_ga(usaphmp_s* h) {
     CK(dalloc(&h->d_cost, 2));
     h->rpart_cap = np;
   }
+  if (!h->d_dist64) CK(dalloc(&h->d_dist64, (size_t)h->p * h->p));
   return USAPHMP_OK;
 }
 
@@ -459,6 +463,7 @@ void usaphmp_destroy(usaphmp_t h) {
   dfree(h->W); dfree(h->C); dfree(h->CTbuf); dfree(h->O); dfree(h->D); dfree(h->Whi); dfree(h->Wlo);
   if (h->tmaps) cudaFree(h->tmaps);
   dfree(h->d_status); dfree(h->d_bad); dfree(h->d_dscratch); dfree(h->d_cost); dfree(h->d_rpart);
+  dfree(h->d_dist64);
   if (h->h_status) cudaFreeHost(h->h_status);
   if (h->h_bad) cudaFreeHost(h->h_bad);
   h->ev.release(); h->ga.release(); h->one.release();
@@ -479,6 +484,8 @@ int usaphmp_set_params(usaphmp_t h, const usaphmp_params* prm) {
   if (prm->n1 < 1) return fail(USAPHMP_EINVAL, "n1 must be >= 1");
   if (prm->path != USAPHMP_PATH_PLAIN_FP32 && prm->path != USAPHMP_PATH_SPLIT_BF16)
     return fail(USAPHMP_EINVAL, "unknown path");
+  if (prm->routing != USAPHMP_ROUTE_DIRECT && prm->routing != USAPHMP_ROUTE_HUB_PATHS)
+    return fail(USAPHMP_EINVAL, "unknown routing");
   h->prm = *prm;
   h->ga_ready = false;
   drop_graph(h);
@@ -718,11 +725,20 @@ int usaphmp_rescore_fp64_dev(usaphmp_t h, int32_t B, const int32_t* hubs, const 
   if (B <= 0) return B == 0 ? USAPHMP_OK : fail(USAPHMP_EINVAL, "B < 0");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   double* part = nullptr;
+  double* dist = nullptr;
   CK(dalloc(&part, (size_t)rescore_parts(h->n) * B));
-  launch_rescore(inst_of(h), B, hubs, slot, part, cost, s);
+  if (h->prm.routing != USAPHMP_ROUTE_DIRECT) {
+    const cudaError_t ea = dalloc(&dist, (size_t)B * h->p * h->p);
+    if (ea != cudaSuccess) {
+      cudaFree(part);
+      return cuda_fail(ea, "dalloc(hub-path tables)");
+    }
+  }
+  launch_rescore(inst_of(h), B, hubs, slot, part, cost, s, dist);
   cudaError_t e = cudaGetLastError();
   cudaError_t e2 = cudaStreamSynchronize(s);
   cudaFree(part);
+  if (dist) cudaFree(dist);
   CK(e);
   CK(e2);
   return USAPHMP_OK;
@@ -828,7 +844,7 @@ int usaphmp_ga_result(usaphmp_t h, usaphmp_result* best, void* stream) {
   TaskSet ts{nullptr, &t1, 1};
   launch_alloc(ts, true, false, s);
   CK(cudaGetLastError());
-  launch_rescore(inst_of(h), 1, h->one.hubs, h->one.slot, h->d_rpart, h->d_cost, s);
+  launch_rescore(inst_of(h), 1, h->one.hubs, h->one.slot, h->d_rpart, h->d_cost, s, h->d_dist64);
   CK(cudaGetLastError());
   std::vector<uint8_t> sl(h->ns);
   double cost = 0;

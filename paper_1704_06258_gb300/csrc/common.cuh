@@ -55,6 +55,7 @@ __host__ __device__ inline bool plain_global_table(int p, int ns) {
 // Immutable per-instance device data.
 struct DevInst {
   int n, p, ldw, ns, nw, symmetric;
+  int routing;  // 0: direct hub arc, 1: shortest paths over open-hub arcs
   float chi, alpha, delta;
   const float* W;
   const float* C;

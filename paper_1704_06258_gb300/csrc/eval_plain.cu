@@ -92,12 +92,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_plain(const __grid_constan
   const float* __restrict__ W = T.in.W;
   const int32_t* __restrict__ hubs = T.pop.hubs;
 
+  // hub-path routing: the allocation kernel left the routed table in chub
+  const bool routed = T.in.routing != 0;
+  const int hst = chub_hstride(p), cst = chub_cstride(p);
   for (int e = threadIdx.x; !gtab && e < KB * pp; e += kThreads) {
     const int bb = e / pp, r = e - bb * pp, k = r / p, l = r - k * p;
     float v = 0.f;
     if (bb < nb) {
       const int32_t* hb = hubs + (long long)(b0 + bb) * p;
-      v = C[(long long)hb[k] * ldw + hb[l]];
+      v = routed ? T.pop.chub[(long long)(b0 + bb) * cst + k * hst + l] : C[(long long)hb[k] * ldw + hb[l]];
     }
     tab[e] = v;
   }

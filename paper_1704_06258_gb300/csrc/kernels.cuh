@@ -109,8 +109,10 @@ void launch_reduce_select(const TaskSet& ts, cudaStream_t s);
 void launch_ga_init(const Task& task, const uint32_t* mask0, const float* fit0, cudaStream_t s);
 
 // rescore.cu: fp64 pair-form objective of B chromosomes of one instance.
+// With in.routing != 0, `dist` (B*p*p doubles of scratch) receives the
+// chromosomes' fp64 hub-path tables first; callers must pass it then.
 void launch_rescore(const DevInst& in, int B, const int32_t* hubs, const uint8_t* slot,
-                    double* part, double* cost, cudaStream_t s);
+                    double* part, double* cost, cudaStream_t s, double* dist = nullptr);
 int rescore_parts(int n);
 
 // capi.cu: records the calling thread's last error message; returns `code`.

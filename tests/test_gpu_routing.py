@@ -1,0 +1,109 @@
+"""Hub-path routing of the transfer leg (eq. 4) on non-metric costs, through
+the C ABI, against the FP64 oracle with routing="hubs"."""
+import zlib
+
+import numpy as np
+import pytest
+
+from gpu_util import dev, host, need_gpu, stream, torch
+from oracle import brute, cost
+from paper_1704_06258_gb300 import synth
+from paper_1704_06258_gb300.binding import (PATH_PLAIN_FP32, PATH_SPLIT_BF16, ROUTE_DIRECT, ROUTE_HUB_PATHS,
+                                            Instance, UsaphmpError)
+
+pytestmark = pytest.mark.gpu
+
+TOL = {PATH_PLAIN_FP32: 1e-5, PATH_SPLIT_BF16: 1e-4}
+PATHS = [PATH_PLAIN_FP32, PATH_SPLIT_BF16]
+
+CASES = {
+    "n200_p10": lambda: synth.latency_like(seed=61, n=200, p=10),
+    "n333_p7_ragged": lambda: synth.latency_like(seed=62, n=333, p=7),
+    "n150_p20": lambda: synth.latency_like(seed=63, n=150, p=20, spread=1.0),
+    "n300_p63": lambda: synth.latency_like(seed=64, n=300, p=63),
+    "n260_p100": lambda: synth.latency_like(seed=65, n=260, p=100),
+    "n12_p1": lambda: synth.latency_like(seed=66, n=12, p=1),
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def oracle_costs(inst, S, routing):
+    return np.array([cost.pair_cost(inst.W, inst.C, inst.chi, inst.alpha, inst.delta, s, routing) for s in S])
+
+
+@pytest.mark.parametrize("path", PATHS, ids=["plain", "split"])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_hub_paths_match_oracle(case, path):
+    inst = CASES[case]()
+    B = 29
+    hubs, S = synth.random_population(zlib.crc32(case.encode()) % 1000, inst.n, inst.p, B)
+    ref = oracle_costs(inst, S, "hubs")
+    direct = oracle_costs(inst, S, "direct")
+    with Instance.from_instance(inst) as gi:
+        gi.set_params(path=path, routing=ROUTE_HUB_PATHS)
+        got = gi.eval(hubs, S)
+        gi.set_params(routing=ROUTE_DIRECT)
+        got_direct = gi.eval(hubs, S)
+    assert (np.abs(got - ref) / ref).max() <= TOL[path]
+    assert (np.abs(got_direct - direct) / direct).max() <= TOL[path]
+    if inst.p > 2:
+        assert (ref < direct * (1 - 1e-6)).any()        # the instance does reward detours
+
+
+@pytest.mark.parametrize("path", PATHS, ids=["plain", "split"])
+def test_hub_paths_change_nothing_on_euclidean_costs(path):
+    inst = synth.urand200(seed=67, n=250, p=12)
+    hubs, S = synth.random_population(68, inst.n, inst.p, 16)
+    with Instance.from_instance(inst) as gi:
+        gi.set_params(path=path)
+        a = gi.eval(hubs, S)
+        gi.set_params(routing=ROUTE_HUB_PATHS)
+        b = gi.eval(hubs, S)
+    np.testing.assert_allclose(b, a, rtol=1e-6)
+
+
+def test_rescore_fp64_with_hub_paths():
+    inst = synth.latency_like(seed=69, n=240, p=9, spread=1.0)
+    B = 5
+    hubs, S = synth.random_population(70, inst.n, inst.p, B)
+    ref = oracle_costs(inst, S, "hubs")
+    with Instance.from_instance(inst) as gi:
+        gi.set_params(routing=ROUTE_HUB_PATHS)
+        hs = np.sort(hubs, axis=1).astype(np.int32)
+        slot = np.full((B, gi.ns), 255, np.uint8)
+        for b in range(B):
+            slot[b, :inst.n] = cost.slots_of(hs[b], S[b])
+        c = torch.empty(B, dtype=torch.float64, device="cuda")
+        d_hs, d_slot = dev(hs), dev(slot)
+        gi.rescore_fp64_dev(B, d_hs.data_ptr(), d_slot.data_ptr(), c.data_ptr(), stream())
+        got = host(c)
+    np.testing.assert_allclose(got, ref, rtol=1e-12)
+
+
+@pytest.mark.parametrize("path", PATHS, ids=["plain", "split"])
+def test_solve_reaches_the_routed_brute_force_nearest_optimum(path):
+    inst = synth.latency_like(seed=71, n=10, p=3, spread=1.0)
+    bf = brute.brute_force(inst.W, inst.C, inst.chi, inst.alpha, inst.delta, inst.p, routing="hubs")
+    direct = brute.brute_force(inst.W, inst.C, inst.chi, inst.alpha, inst.delta, inst.p)
+    assert bf["nearest"][0] < direct["nearest"][0]
+    with Instance.from_instance(inst) as gi:
+        gi.set_params(islands=1, island_size=64, n1=10, path=path, routing=ROUTE_HUB_PATHS)
+        r = gi.solve(100, 2024)
+    assert r["cost_fp64"] == pytest.approx(bf["nearest"][0], rel=1e-12)
+    cost.check_allocation(inst.n, r["hubs"], r["S"])
+    assert r["cost_fp64"] == pytest.approx(
+        cost.pair_cost(inst.W, inst.C, inst.chi, inst.alpha, inst.delta, r["S"], "hubs"), rel=1e-12)
+    assert abs(r["cost_fp32"] - r["cost_fp64"]) / r["cost_fp64"] <= TOL[path]
+
+
+def test_unknown_routing_is_refused():
+    inst = synth.latency_like(seed=72, n=20, p=3)
+    with Instance.from_instance(inst) as gi:
+        with pytest.raises(UsaphmpError) as e:
+            gi.set_params(routing=2)
+        assert e.value.name == "EINVAL"
+        assert gi.params["routing"] == ROUTE_DIRECT
