@@ -297,6 +297,28 @@ def large_n_leg(steps, warmup, flush, stream):
     return res
 
 
+def routing_leg(steps, warmup, flush, stream):
+    """Hub-path routing (eq. 4) on a non-metric latency-like instance of the
+    bench size (n=1000, p=20, population 4096): generations/s of the split
+    path with Floyd-Warshall routing and with the direct arc on the same
+    instance, and the error of both evaluators against the fp64 rescoring."""
+    from paper_1704_06258_gb300 import synth
+    from paper_1704_06258_gb300.binding import PATH_SPLIT_BF16, ROUTE_DIRECT, ROUTE_HUB_PATHS, Instance
+    inst = synth.latency_like(seed=1006, n=N, p=P_HUBS)
+    out = {"workload": f"latency-like non-metric n={N} p={P_HUBS} (Euclidean x lognormal(0,0.6) per pair), "
+                       f"population {ISLANDS * ISLAND}"}
+    with Instance.from_instance(inst) as gi:
+        for name, routing in (("hub_paths", ROUTE_HUB_PATHS), ("direct", ROUTE_DIRECT)):
+            gi.set_params(islands=ISLANDS, island_size=ISLAND, n1=10, path=PATH_SPLIT_BF16, routing=routing)
+            st, _, res = timed_generations(gi, steps, warmup, flush, stream, 1)
+            out[name] = {"evals_per_s": ISLANDS * ISLAND / (st["generation"] * 1e-3), "ms_per_step": st["generation"],
+                         "allocation_ms": st["allocation"], "transfer_ms": st["transfer"],
+                         "best_cost_fp64": res["cost_fp64"]}
+            if routing == ROUTE_HUB_PATHS:
+                out["rel_err_vs_fp64"] = rel_error_sample(gi, inst, count=32)
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_1704_06258_gb300 import synth
@@ -325,6 +347,7 @@ def run_ours(args):
         e2e = None if only_split else e2e_eval(gi, inst, steps=max(3, min(50, args.steps // 20)), warmup=1)
         rel_err = None if only_split else rel_error_sample(gi, inst)
     large = large_n_leg(20, 3, flush, stream) if (not only_split and world == 1 and args.large) else None
+    routed = routing_leg(200, 3, flush, stream) if (not only_split and world == 1 and args.large) else None
     if only_split:
         plain = dict(split)
     ms0 = split["generation"]
@@ -375,6 +398,7 @@ def run_ours(args):
         "split_vs_plain": plain_ms / ms,
         "rel_err_vs_fp64": rel_err,
         "large_n": large,
+        "routing_hub_paths": routed,
         "p50_solve_ms": serving["p50_ms"] if serving else None,
         "p99_solve_ms": serving["p99_ms"] if serving else None,
         "serving": serving,
