@@ -319,6 +319,32 @@ def routing_leg(steps, warmup, flush, stream):
     return out
 
 
+def factor_sweep():
+    """The study of §6.2 (Fig. 3) on a synthetic 25-node instance (the CAB
+    data set has 25 cities but is not available): for collection and
+    distribution factors chi = delta and hub discounts alpha, the GA's best
+    solution (p = 3, 4 islands x 64, 200 generations) and the average cost of
+    its hub-to-hub arcs (mean of C over pairs of distinct open hubs),
+    objective reported per unit of flow as §4.3 does for CAB."""
+    from paper_1704_06258_gb300 import synth
+    from paper_1704_06258_gb300.binding import PATH_SPLIT_BF16, SCALE_PER_FLOW, Instance
+    inst = synth.urand200(seed=1007, n=25, p=3)
+    C = inst.C.astype(np.float64)
+    rows = []
+    t0 = time.perf_counter()
+    for cd in (0.5, 1.0, 2.0, 3.0):
+        for alpha in (0.2, 0.4, 0.6, 0.8, 1.0):
+            with Instance(inst.W, inst.C, inst.p, chi=cd, alpha=alpha, delta=cd) as gi:
+                gi.set_params(islands=4, island_size=64, n1=10, path=PATH_SPLIT_BF16, scale=SCALE_PER_FLOW)
+                r = gi.solve(200, 2024)
+            hb = np.sort(r["hubs"])
+            pairs = [C[a, b] for i, a in enumerate(hb) for b in hb[i + 1:]]
+            rows.append({"chi_delta": cd, "alpha": alpha, "hubs": hb.tolist(),
+                         "avg_interhub": float(np.mean(pairs)), "cost_per_flow": r["cost_fp64"]})
+    return {"instance": "25 nodes uniform in [0,1000]^2, W lognormal(0,1), p=3", "rows": rows,
+            "wall_s": time.perf_counter() - t0}
+
+
 def run_ours(args):
     import torch
     from paper_1704_06258_gb300 import synth
@@ -348,6 +374,7 @@ def run_ours(args):
         rel_err = None if only_split else rel_error_sample(gi, inst)
     large = large_n_leg(20, 3, flush, stream) if (not only_split and world == 1 and args.large) else None
     routed = routing_leg(200, 3, flush, stream) if (not only_split and world == 1 and args.large) else None
+    sweep = factor_sweep() if (not only_split and world == 1 and args.large) else None
     if only_split:
         plain = dict(split)
     ms0 = split["generation"]
@@ -399,6 +426,7 @@ def run_ours(args):
         "rel_err_vs_fp64": rel_err,
         "large_n": large,
         "routing_hub_paths": routed,
+        "factor_sweep": sweep,
         "p50_solve_ms": serving["p50_ms"] if serving else None,
         "p99_solve_ms": serving["p99_ms"] if serving else None,
         "serving": serving,

@@ -60,6 +60,20 @@ enum {
   USAPHMP_ROUTE_HUB_PATHS = 1
 };
 
+/* Scale of the objective values returned to the caller (§4.3: the CAB
+ * benchmarks report the cost per unit of flow, the AP/Urand ones the cost
+ * times 10^-3, PlanetLab the raw cost).  It multiplies the fitness written by
+ * usaphmp_eval / _eval_dev / _eval_slots_dev (in fp32), the costs of
+ * usaphmp_rescore_fp64_dev (in fp64) and both costs of a result; the GA
+ * selects on the raw cost, so the search is the same for every scale.
+ * PER_FLOW divides by sum_ij W[i][j] (computed in fp64 at creation; refused
+ * when it is 0). */
+enum {
+  USAPHMP_SCALE_RAW = 0,
+  USAPHMP_SCALE_MILLI = 1,
+  USAPHMP_SCALE_PER_FLOW = 2
+};
+
 /* Evaluators of the transfer term. */
 enum {
   USAPHMP_PATH_PLAIN_FP32 = 0,  /* fp32 CUDA cores, shared-memory gather of C[h(i)][h(j)] */
@@ -81,6 +95,7 @@ typedef struct {
                            evaluation, generation and fp64 rescoring of the
                            handle (the server and the allocation-free entry
                            point use DIRECT) */
+  int32_t scale;        /* USAPHMP_SCALE_* (default RAW) */
 } usaphmp_params;
 
 typedef struct {

@@ -119,6 +119,19 @@ def pair_cost(W, C, chi, alpha, delta, h, routing="direct"):
     return math.fsum(np.sum(per_pair, axis=1))
 
 
+def scaled_cost(value, W, scale="raw"):
+    """The fitness as the benchmarks of §4.3 report it: "raw" (PlanetLab),
+    "milli" (the cost times 10^-3, AP and Urand) or "per_flow" (the cost
+    divided by the total flow sum_ij W[i,j], CAB)."""
+    if scale == "raw":
+        return float(value)
+    if scale == "milli":
+        return float(value) * 1e-3
+    if scale == "per_flow":
+        return float(value) / math.fsum(_f64(W).ravel())
+    raise ValueError(scale)
+
+
 def three_term_cost(W, C, chi, alpha, delta, hubs, h, routing="direct"):
     """The same objective regrouped as the GPU evaluates it.
 

@@ -22,6 +22,9 @@ PATH_PLAIN_FP32 = 0
 PATH_SPLIT_BF16 = 1
 ROUTE_DIRECT = 0
 ROUTE_HUB_PATHS = 1
+SCALE_RAW = 0
+SCALE_MILLI = 1
+SCALE_PER_FLOW = 2
 
 ERRORS = {-1: "EINVAL", -2: "EINVAL_CHROM", -3: "ENOMEM", -4: "ECUDA", -5: "ETIMEOUT", -6: "EBUSY", -7: "EIO"}
 
@@ -31,7 +34,7 @@ c_i32, c_i64, c_u64, c_f64, c_f32, c_vp = (ctypes.c_int32, ctypes.c_int64, ctype
 
 class Params(ctypes.Structure):
     _fields_ = [("islands", c_i32), ("island_size", c_i32), ("n1", c_i32), ("path", c_i32),
-                ("elitist", c_i32), ("use_graph", c_i32), ("routing", c_i32)]
+                ("elitist", c_i32), ("use_graph", c_i32), ("routing", c_i32), ("scale", c_i32)]
 
 
 class Result(ctypes.Structure):

@@ -101,6 +101,8 @@ struct usaphmp_s {
   double* d_rpart = nullptr;
   int rpart_cap = 0;
   double* d_dist64 = nullptr;  // p*p fp64 hub-path table of the returned solution (hub-path routing)
+  double* d_total = nullptr;   // sum of W, fp64 (device)
+  double total_flow = 0.0;     // the same on the host
   // evaluation workspace and host-call staging
   Pop ev;
   int32_t* d_hubs_in = nullptr;
@@ -135,6 +137,7 @@ DevInst inst_of(const usaphmp_s* h) {
   in.symmetric = h->symmetric;
   in.routing = h->prm.routing;
   in.chi = (float)h->chi; in.alpha = (float)h->alpha; in.delta = (float)h->delta;
+  in.chi_d = h->chi; in.alpha_d = h->alpha; in.delta_d = h->delta;
   in.W = h->W; in.C = h->C; in.CT = h->symmetric ? h->C : h->CTbuf;
   in.O = h->O; in.D = h->D; in.Whi = h->Whi; in.Wlo = h->Wlo;
   return in;
@@ -177,7 +180,17 @@ PopBuf popbuf(const usaphmp_s* h, const Pop& P, int B) {
   pb.hubs_in = nullptr;
   pb.slot_in = nullptr;
   pb.status = h->d_status;
+  pb.out_scale = 1.0f;
   return pb;
+}
+
+// Factor of §4.3 applied to objective values returned to the caller.
+double output_scale(const usaphmp_s* h) {
+  switch (h->prm.scale) {
+    case USAPHMP_SCALE_MILLI: return 1e-3;
+    case USAPHMP_SCALE_PER_FLOW: return 1.0 / h->total_flow;
+    default: return 1.0;
+  }
 }
 
 Task make_task(const usaphmp_s* h, const PopBuf& pb) {
@@ -272,6 +285,7 @@ int create_common(usaphmp_s* h, const float* W, const float* C, bool dev, cudaSt
   CK(dalloc(&h->d_status, 1));
   CK(dalloc(&h->d_bad, 1));
   CK(dalloc(&h->d_dscratch, n));
+  CK(dalloc(&h->d_total, 1));
   CK(cudaMallocHost(&h->h_status, sizeof(uint32_t)));
   CK(cudaMallocHost(&h->h_bad, sizeof(int)));
   if (!dev) s = h->stream;
@@ -284,6 +298,8 @@ int create_common(usaphmp_s* h, const float* W, const float* C, bool dev, cudaSt
   launch_check_values(h->W, h->C, n, h->ldw, h->d_status, s);
   launch_split_bf16(h->W, h->Whi, h->Wlo, (long long)mat, s);
   launch_flows(h->W, n, h->ldw, h->O, h->D, s);
+  launch_total_flow(h->W, n, h->ldw, h->d_dscratch, h->d_total, s);
+  CK(cudaMemcpyAsync(&h->total_flow, h->d_total, sizeof(double), cudaMemcpyDeviceToHost, s));
   uint32_t* d_asym = reinterpret_cast<uint32_t*>(h->d_bad);  // reuse as a flag
   CK(cudaMemsetAsync(d_asym, 0, sizeof(uint32_t), s));
   launch_asymmetry(h->C, n, h->ldw, d_asym, s);
@@ -326,6 +342,7 @@ int create_impl(int32_t n, int32_t p, const float* W, const float* C, double chi
   h->prm.elitist = 0;
   h->prm.use_graph = 1;
   h->prm.routing = USAPHMP_ROUTE_DIRECT;
+  h->prm.scale = USAPHMP_SCALE_RAW;
   const int r = create_common(h, W, C, dev, static_cast<cudaStream_t>(stream));
   if (r != USAPHMP_OK) {
     const std::string msg = g_err;
@@ -351,6 +368,7 @@ int eval_canonical(usaphmp_s* h, int B, const int32_t* hubs_in, const int32_t* S
   CK(cudaGetLastError());
   PopBuf pb = popbuf(h, h->ev, B);
   pb.fit = fit_out;
+  pb.out_scale = (float)output_scale(h);
   const Task task = make_task(h, pb);
   RET(run_eval(h, task, false, s));
   return check_status(h, s, "usaphmp_eval");
@@ -463,7 +481,7 @@ void usaphmp_destroy(usaphmp_t h) {
   dfree(h->W); dfree(h->C); dfree(h->CTbuf); dfree(h->O); dfree(h->D); dfree(h->Whi); dfree(h->Wlo);
   if (h->tmaps) cudaFree(h->tmaps);
   dfree(h->d_status); dfree(h->d_bad); dfree(h->d_dscratch); dfree(h->d_cost); dfree(h->d_rpart);
-  dfree(h->d_dist64);
+  dfree(h->d_dist64); dfree(h->d_total);
   if (h->h_status) cudaFreeHost(h->h_status);
   if (h->h_bad) cudaFreeHost(h->h_bad);
   h->ev.release(); h->ga.release(); h->one.release();
@@ -486,6 +504,10 @@ int usaphmp_set_params(usaphmp_t h, const usaphmp_params* prm) {
     return fail(USAPHMP_EINVAL, "unknown path");
   if (prm->routing != USAPHMP_ROUTE_DIRECT && prm->routing != USAPHMP_ROUTE_HUB_PATHS)
     return fail(USAPHMP_EINVAL, "unknown routing");
+  if (prm->scale != USAPHMP_SCALE_RAW && prm->scale != USAPHMP_SCALE_MILLI && prm->scale != USAPHMP_SCALE_PER_FLOW)
+    return fail(USAPHMP_EINVAL, "unknown scale");
+  if (prm->scale == USAPHMP_SCALE_PER_FLOW && !(h->total_flow > 0.0))
+    return fail(USAPHMP_EINVAL, "scale per unit flow needs a positive total flow");
   h->prm = *prm;
   h->ga_ready = false;
   drop_graph(h);
@@ -693,6 +715,7 @@ int usaphmp_eval_slots_dev(usaphmp_t h, int32_t B, const int32_t* hubs, const ui
   pb.hubs_in = hubs;
   pb.slot_in = slot;
   pb.fit = fitness;
+  pb.out_scale = (float)output_scale(h);
   const Task t = make_task(h, pb);
   return run_eval(h, t, false, s);
 }
@@ -734,7 +757,7 @@ int usaphmp_rescore_fp64_dev(usaphmp_t h, int32_t B, const int32_t* hubs, const 
       return cuda_fail(ea, "dalloc(hub-path tables)");
     }
   }
-  launch_rescore(inst_of(h), B, hubs, slot, part, cost, s, dist);
+  launch_rescore(inst_of(h), B, hubs, slot, part, cost, s, dist, output_scale(h));
   cudaError_t e = cudaGetLastError();
   cudaError_t e2 = cudaStreamSynchronize(s);
   cudaFree(part);
@@ -844,7 +867,8 @@ int usaphmp_ga_result(usaphmp_t h, usaphmp_result* best, void* stream) {
   TaskSet ts{nullptr, &t1, 1};
   launch_alloc(ts, true, false, s);
   CK(cudaGetLastError());
-  launch_rescore(inst_of(h), 1, h->one.hubs, h->one.slot, h->d_rpart, h->d_cost, s, h->d_dist64);
+  launch_rescore(inst_of(h), 1, h->one.hubs, h->one.slot, h->d_rpart, h->d_cost, s, h->d_dist64,
+                 output_scale(h));
   CK(cudaGetLastError());
   std::vector<uint8_t> sl(h->ns);
   double cost = 0;
@@ -855,7 +879,7 @@ int usaphmp_ga_result(usaphmp_t h, usaphmp_result* best, void* stream) {
   if (best->S)
     for (int i = 0; i < h->n; ++i) best->S[i] = hubs[sl[i]];
   best->cost_fp64 = cost;
-  best->cost_fp32 = bf;
+  best->cost_fp32 = (float)(bf * output_scale(h));
   best->evals = h->ga_evals;
   return USAPHMP_OK;
 }

@@ -56,7 +56,8 @@ __host__ __device__ inline bool plain_global_table(int p, int ns) {
 struct DevInst {
   int n, p, ldw, ns, nw, symmetric;
   int routing;  // 0: direct hub arc, 1: shortest paths over open-hub arcs
-  float chi, alpha, delta;
+  float chi, alpha, delta;                // for the fp32 and split-bf16 paths
+  double chi_d, alpha_d, delta_d;         // as given, for the fp64 rescoring
   const float* W;
   const float* C;
   const float* CT;
@@ -83,6 +84,7 @@ struct PopBuf {
   int npart;       // number of partial rows: part[r][b], r < npart
   float* fit;      // fp32 fitness
   uint32_t* status;  // device status word (kStatus* bits)
+  float out_scale;   // factor k_reduce applies to the fitness it writes (1: raw cost)
 };
 
 // Island GA state (§5): R islands of P chromosomes.

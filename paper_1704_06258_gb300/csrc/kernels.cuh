@@ -55,6 +55,8 @@ inline TaskParam make_param(const TaskSet& ts) {
 void launch_check_values(const float* W, const float* C, int n, int ldw, uint32_t* status, cudaStream_t s);
 void launch_split_bf16(const float* W, __nv_bfloat16* Whi, __nv_bfloat16* Wlo, long long total, cudaStream_t s);
 void launch_flows(const float* W, int n, int ldw, float* O, float* D, cudaStream_t s);
+// *out = sum of all W entries in fp64 (rows: n doubles of scratch).
+void launch_total_flow(const float* W, int n, int ldw, double* rows, double* out, cudaStream_t s);
 void launch_asymmetry(const float* C, int n, int ldw, uint32_t* flag, cudaStream_t s);
 void launch_transpose(const float* C, float* CT, int n, int ldw, cudaStream_t s);
 void launch_middle_nodes(const float* C, int n, int ldw, int p, double* dscratch, uint32_t* mask,
@@ -112,7 +114,7 @@ void launch_ga_init(const Task& task, const uint32_t* mask0, const float* fit0, 
 // With in.routing != 0, `dist` (B*p*p doubles of scratch) receives the
 // chromosomes' fp64 hub-path tables first; callers must pass it then.
 void launch_rescore(const DevInst& in, int B, const int32_t* hubs, const uint8_t* slot,
-                    double* part, double* cost, cudaStream_t s, double* dist = nullptr);
+                    double* part, double* cost, cudaStream_t s, double* dist = nullptr, double scale = 1.0);
 int rescore_parts(int n);
 
 // capi.cu: records the calling thread's last error message; returns `code`.

@@ -62,6 +62,7 @@ extern "C" int usaphmp_rescore_fp64_noalloc(int32_t n, int32_t p, int32_t B, con
   DevInst in{};
   in.n = n; in.p = p; in.ldw = n; in.ns = n; in.nw = (n + 31) / 32; in.symmetric = 0;
   in.chi = (float)chi; in.alpha = (float)alpha; in.delta = (float)delta;
+  in.chi_d = chi; in.alpha_d = alpha; in.delta_d = delta;
   in.W = W; in.C = C; in.CT = C;
   launch_rescore(in, B, hubs, slot, scratch, cost, static_cast<cudaStream_t>(stream));
   const cudaError_t e = cudaGetLastError();

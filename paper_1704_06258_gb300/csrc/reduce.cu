@@ -1,7 +1,8 @@
 // Fitness assembly: fit_b = t12_b + alpha * T3_b, with T3_b the sum of the
 // evaluator's partial transfer sums part[r][b] taken in a fixed order (r
 // ascending), so a chromosome's fitness does not depend on the launch it was
-// evaluated in.
+// evaluated in; times the output scale of §4.3 (1, 10^-3 or 1/sum W) for
+// values returned to the caller.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -16,7 +17,7 @@ __global__ void k_reduce(const __grid_constant__ TaskParam tp) {
   const float* __restrict__ part = T.pop.part + b;
   float s = 0.f;
   for (int r = 0; r < T.pop.npart; ++r) s += part[(long long)r * B];
-  T.pop.fit[b] = T.pop.t12[b] + T.in.alpha * s;
+  T.pop.fit[b] = (T.pop.t12[b] + T.in.alpha * s) * T.pop.out_scale;
 }
 
 void launch_reduce(const TaskSet& ts, cudaStream_t s) {

@@ -1,6 +1,7 @@
 // FP64 rescoring of chromosomes by the pair form of objective (1), §3:
 //   cost = sum_i sum_j W[i][j] * (chi*C[i,h(i)] + alpha*T[h(i),h(j)] + delta*C[h(j),j]),
-// every product and sum in fp64 from the fp32 instance values, with T = C
+// every product and sum in fp64 from the fp32 instance values and the fp64
+// factors chi, alpha, delta as the caller gave them, with T = C
 // (direct hub arc) or, for hub-path routing (eq. 4), T = the cheapest path
 // over arcs between the chromosome's open hubs (Floyd-Warshall in fp64,
 // zero on the diagonal).  It shares no arithmetic with the fp32 and
@@ -61,7 +62,7 @@ __global__ void __launch_bounds__(256) k_rescore_part(DevInst in, const int32_t*
   const uint8_t* sl = slot + (long long)b * in.ns;
   const int chunk = (n + nparts - 1) / nparts;
   const int i0 = part_idx * chunk, i1 = min(n, i0 + chunk);
-  const double chi = in.chi, alpha = in.alpha, delta = in.delta;
+  const double chi = in.chi_d, alpha = in.alpha_d, delta = in.delta_d;
   const double* db = dist ? dist + (long long)b * p * p : nullptr;
   double s = 0.0;
   for (int i = i0; i < i1; ++i) {
@@ -80,24 +81,25 @@ __global__ void __launch_bounds__(256) k_rescore_part(DevInst in, const int32_t*
   if (threadIdx.x == 0) part[(long long)b * nparts + part_idx] = s;
 }
 
-__global__ void k_rescore_final(const double* __restrict__ part, int nparts, int B, double* __restrict__ cost) {
+__global__ void k_rescore_final(const double* __restrict__ part, int nparts, int B, double scale,
+                                double* __restrict__ cost) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
   double s = 0.0;
   for (int k = 0; k < nparts; ++k) s += part[(long long)b * nparts + k];
-  cost[b] = s;
+  cost[b] = s * scale;
 }
 
 int rescore_parts(int n) { return n < kParts ? n : kParts; }
 
 void launch_rescore(const DevInst& in, int B, const int32_t* hubs, const uint8_t* slot,
-                    double* part, double* cost, cudaStream_t s, double* dist) {
+                    double* part, double* cost, cudaStream_t s, double* dist, double scale) {
   if (B <= 0) return;
   const int np = rescore_parts(in.n);
   const bool routed = in.routing != 0 && dist != nullptr;
   if (routed) k_hub_paths64<<<B, 256, 0, s>>>(in, hubs, dist);
   k_rescore_part<<<dim3(np, B), 256, 0, s>>>(in, hubs, slot, routed ? dist : nullptr, part);
-  k_rescore_final<<<(B + 127) / 128, 128, 0, s>>>(part, np, B, cost);
+  k_rescore_final<<<(B + 127) / 128, 128, 0, s>>>(part, np, B, scale, cost);
 }
 
 }  // namespace usaphmp

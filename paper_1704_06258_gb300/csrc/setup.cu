@@ -43,6 +43,25 @@ __global__ void k_row_flows(const float* __restrict__ W, int n, int ldw, float* 
   if (threadIdx.x == 0) O[i] = (float)s;
 }
 
+// Total flow sum_i sum_j W[i][j] in fp64: row sums (one block per row), then
+// one block adds the rows; the divisor of the per-unit-flow fitness of §4.3.
+__global__ void k_row_sums64(const float* __restrict__ W, int n, int ldw, double* __restrict__ rows) {
+  __shared__ double red[32];
+  const int i = blockIdx.x;
+  double s = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) s += (double)W[(long long)i * ldw + j];
+  s = block_sum_f64(s, red);
+  if (threadIdx.x == 0) rows[i] = s;
+}
+
+__global__ void k_sum64(const double* __restrict__ x, int n, double* __restrict__ out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += x[i];
+  s = block_sum_f64(s, red);
+  if (threadIdx.x == 0) *out = s;
+}
+
 // D_j = sum_i W[i][j] (one thread per column, coalesced over j).
 __global__ void k_col_flows(const float* __restrict__ W, int n, int ldw, float* __restrict__ D) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -143,6 +162,11 @@ void launch_check_values(const float* W, const float* C, int n, int ldw, uint32_
 
 void launch_split_bf16(const float* W, __nv_bfloat16* Whi, __nv_bfloat16* Wlo, long long total, cudaStream_t s) {
   k_split_bf16<<<grid_for(total, 256), 256, 0, s>>>(W, Whi, Wlo, total);
+}
+
+void launch_total_flow(const float* W, int n, int ldw, double* rows, double* out, cudaStream_t s) {
+  k_row_sums64<<<n, 256, 0, s>>>(W, n, ldw, rows);
+  k_sum64<<<1, 256, 0, s>>>(rows, n, out);
 }
 
 void launch_flows(const float* W, int n, int ldw, float* O, float* D, cudaStream_t s) {

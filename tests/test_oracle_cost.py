@@ -48,6 +48,11 @@ def test_hand4_costs_terms_flows(golden_dir):
             h = cost.nearest_allocation(C, hubs)
             _, tc, td, tt = cost.three_term_cost(W, C, chi, alpha, delta, hubs, h)
             assert (tc, td, tt) == (float(r[2]), float(r[3]), float(r[4]))
+        elif r[0] == "scaled":
+            h, mode, val = _ints(r[2]), r[3], float(r[4])
+            raw = cost.pair_cost(W, C, chi, alpha, delta, h)
+            assert cost.scaled_cost(raw, W, mode) == pytest.approx(val, rel=1e-15)
+            assert cost.scaled_cost(raw, W, "raw") == raw
         elif r[0] == "middle":
             np.testing.assert_array_equal(cost.middle_nodes(C, int(r[1])), _ints(r[2]))
 
