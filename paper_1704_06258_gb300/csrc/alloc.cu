@@ -13,7 +13,15 @@
 #include "common.cuh"
 #include "kernels.cuh"
 
+#include <algorithm>
+
 namespace usaphmp {
+
+namespace {
+// Hub-path tables up to this many entries (p <= 110) are relaxed in shared
+// memory; larger ones in place in global memory.
+constexpr int kFwSmemEntries = 12288;
+}
 
 template <bool kNearest>
 __global__ void __launch_bounds__(256) k_alloc(const __grid_constant__ TaskParam tp, int with_chub) {
@@ -93,14 +101,68 @@ __global__ void __launch_bounds__(256) k_alloc(const __grid_constant__ TaskParam
       // Pass m relaxes every (a, c) through hub m.  Row m and column m do not
       // change during pass m (their diagonal entry is 0 and costs are >= 0),
       // so the in-place updates of one pass do not race.
+      extern __shared__ float fw[];
+      const bool in_smem = p * p <= kFwSmemEntries;
       __syncthreads();
-      for (int m = 0; m < p; ++m) {
-        for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+      if (in_smem && p * p <= 4 * 256 && blockDim.x == 256) {
+        // p <= 32: every thread owns up to 4 entries and keeps them in
+        // registers; shared memory holds the table for the others' reads.
+        float v[4];
+        int e4[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int e = threadIdx.x + 256 * k;
           const int a = e / p, c = e - a * p;
-          const float v = ch[a * hst + m] + ch[m * hst + c];
-          if (v < ch[a * hst + c]) ch[a * hst + c] = v;
+          e4[k] = e < p * p ? e : -1;
+          v[k] = e < p * p ? ch[a * hst + c] : 0.f;
+          if (e < p * p) fw[e] = v[k];
         }
         __syncthreads();
+        int ra[4], rc[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          ra[k] = e4[k] >= 0 ? e4[k] / p : 0;
+          rc[k] = e4[k] >= 0 ? e4[k] - ra[k] * p : 0;
+        }
+        for (int m = 0; m < p; ++m) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            if (e4[k] >= 0) {
+              const float nv = fw[ra[k] * p + m] + fw[m * p + rc[k]];
+              if (nv < v[k]) {
+                v[k] = nv;
+                fw[e4[k]] = nv;
+              }
+            }
+          }
+          __syncthreads();
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (e4[k] >= 0) ch[ra[k] * hst + rc[k]] = v[k];
+      } else {
+        // warp w relaxes rows w, w + nwarps, ...; lane l columns l, l + 32, ...
+        float* d = in_smem ? fw : ch;
+        const int ld = in_smem ? p : hst;
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+        if (in_smem) {
+          for (int a = wid; a < p; a += nwarp)
+            for (int c = lane; c < p; c += 32) fw[a * p + c] = ch[a * hst + c];
+          __syncthreads();
+        }
+        for (int m = 0; m < p; ++m) {
+          for (int a = wid; a < p; a += nwarp) {
+            const float dam = d[a * ld + m];
+            for (int c = lane; c < p; c += 32) {
+              const float nv = dam + d[m * ld + c];
+              if (nv < d[a * ld + c]) d[a * ld + c] = nv;
+            }
+          }
+          __syncthreads();
+        }
+        if (in_smem)
+          for (int a = wid; a < p; a += nwarp)
+            for (int c = lane; c < p; c += 32) ch[a * hst + c] = fw[a * p + c];
       }
     }
   }
@@ -111,10 +173,15 @@ void launch_alloc(const TaskSet& ts, bool nearest, bool with_chub, cudaStream_t 
   for (int t = 0; t < ts.count; ++t) tp.bo.o[t + 1] = tp.bo.o[t] + ts.h[t].pop.B;
   const int blocks = tp.bo.o[ts.count];
   if (blocks == 0) return;
+  size_t smem = 0;
+  for (int t = 0; t < ts.count; ++t) {
+    const int p = ts.h[t].in.p;
+    if (ts.h[t].in.routing && p * p <= kFwSmemEntries) smem = std::max(smem, (size_t)p * p * sizeof(float));
+  }
   if (nearest)
-    k_alloc<true><<<blocks, 256, 0, s>>>(tp, with_chub ? 1 : 0);
+    k_alloc<true><<<blocks, 256, smem, s>>>(tp, with_chub ? 1 : 0);
   else
-    k_alloc<false><<<blocks, 256, 0, s>>>(tp, with_chub ? 1 : 0);
+    k_alloc<false><<<blocks, 256, smem, s>>>(tp, with_chub ? 1 : 0);
 }
 
 }  // namespace usaphmp

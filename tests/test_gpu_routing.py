@@ -22,6 +22,7 @@ CASES = {
     "n150_p20": lambda: synth.latency_like(seed=63, n=150, p=20, spread=1.0),
     "n300_p63": lambda: synth.latency_like(seed=64, n=300, p=63),
     "n260_p100": lambda: synth.latency_like(seed=65, n=260, p=100),
+    "n300_p150_global_table": lambda: synth.latency_like(seed=73, n=300, p=150),
     "n12_p1": lambda: synth.latency_like(seed=66, n=12, p=1),
 }
 
