@@ -96,6 +96,10 @@ typedef struct {
                            handle (the server and the allocation-free entry
                            point use DIRECT) */
   int32_t scale;        /* USAPHMP_SCALE_* (default RAW) */
+  int32_t local_search; /* >= 0 (default 0): sweeps of the allocation local
+                           search (usaphmp_local_search_dev) applied to the
+                           returned solution; the GA itself evaluates nearest
+                           allocations */
 } usaphmp_params;
 
 typedef struct {
@@ -176,6 +180,23 @@ int usaphmp_select_dev(usaphmp_t h, int32_t R, int32_t P, int32_t g, const uint3
                        float* best_fit, void* stream);
 
 /* FP64 objective (pair form of eq. 1) of B canonical chromosomes: cost [B]. */
+/* Allocation local search for fixed hubs, in fp64 (§4.1 allocates every
+ * spoke to its nearest hub, which is not always the cheapest allocation for
+ * those hubs).  A sweep visits the spokes in ascending node order and moves
+ * spoke i to the open hub whose choice lowers objective (1) the most (the
+ * lowest node id among equal changes), when the change is negative, before
+ * visiting the next spoke; sweeps repeat until one moves nothing or
+ * max_sweeps (>= 1) have run.  Hubs keep serving themselves.  Uses the
+ * handle's routing.
+ *   hubs  i32 [B][p] ascending node ids (device)
+ *   slot  u8  [B][ns] (device, in/out): rank in hubs of each node's hub,
+ *         a valid single allocation on entry (every hub in its own slot)
+ *   moves, sweeps  i32 [B] out (device, may be NULL): moves made, sweeps run
+ * Allocates B * (2*n*p + p*p) doubles of scratch for the call and
+ * synchronises `stream` before returning. */
+int usaphmp_local_search_dev(usaphmp_t h, int32_t B, const int32_t* hubs, uint8_t* slot, int32_t max_sweeps,
+                             int32_t* moves, int32_t* sweeps, void* stream);
+
 int usaphmp_rescore_fp64_dev(usaphmp_t h, int32_t B, const int32_t* hubs, const uint8_t* slot,
                              double* cost, void* stream);
 

@@ -34,7 +34,8 @@ c_i32, c_i64, c_u64, c_f64, c_f32, c_vp = (ctypes.c_int32, ctypes.c_int64, ctype
 
 class Params(ctypes.Structure):
     _fields_ = [("islands", c_i32), ("island_size", c_i32), ("n1", c_i32), ("path", c_i32),
-                ("elitist", c_i32), ("use_graph", c_i32), ("routing", c_i32), ("scale", c_i32)]
+                ("elitist", c_i32), ("use_graph", c_i32), ("routing", c_i32), ("scale", c_i32),
+                ("local_search", c_i32)]
 
 
 class Result(ctypes.Structure):
@@ -83,6 +84,7 @@ _SIGS = {
     "usaphmp_server_poll": (c_i32, [c_vp, c_i64, ctypes.POINTER(Result)]),
     "usaphmp_server_footprint": (c_i32, [c_i32, c_i32, c_i32, c_i32, ctypes.POINTER(c_i64)]),
     "usaphmp_server_destroy": (None, [c_vp]),
+    "usaphmp_local_search_dev": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp]),
     "usaphmp_set_tile": (c_i32, [c_vp, ctypes.POINTER(Tile)]),
     "usaphmp_get_tile": (c_i32, [c_vp, ctypes.POINTER(Tile)]),
     "usaphmp_autotune": (c_i32, [c_vp, c_i32, ctypes.c_char_p, ctypes.POINTER(Tile), ctypes.POINTER(c_f64),
@@ -270,6 +272,10 @@ class Instance:
     def select_dev(self, R, P, g, mask_ptr, fit_ptr, anc_ptr, anc_fit_ptr, best_ptr, best_fit_ptr, stream=0):
         check(lib().usaphmp_select_dev(self.h, R, P, g, mask_ptr, fit_ptr, anc_ptr, anc_fit_ptr, best_ptr,
                                        best_fit_ptr, stream))
+
+    def local_search_dev(self, B, hubs_ptr, slot_ptr, max_sweeps, moves_ptr=None, sweeps_ptr=None, stream=0):
+        check(lib().usaphmp_local_search_dev(self.h, B, hubs_ptr, slot_ptr, max_sweeps, moves_ptr, sweeps_ptr,
+                                             stream))
 
     def rescore_fp64_dev(self, B, hubs_ptr, slot_ptr, cost_ptr, stream=0):
         check(lib().usaphmp_rescore_fp64_dev(self.h, B, hubs_ptr, slot_ptr, cost_ptr, stream))

@@ -102,6 +102,8 @@ struct usaphmp_s {
   int rpart_cap = 0;
   double* d_dist64 = nullptr;  // p*p fp64 hub-path table of the returned solution (hub-path routing)
   double* d_total = nullptr;   // sum of W, fp64 (device)
+  double* d_ls = nullptr;      // local-search scratch of the returned solution
+  int32_t* d_ls_count = nullptr;  // its moves and sweeps
   double total_flow = 0.0;     // the same on the host
   // evaluation workspace and host-call staging
   Pop ev;
@@ -343,6 +345,7 @@ int create_impl(int32_t n, int32_t p, const float* W, const float* C, double chi
   h->prm.use_graph = 1;
   h->prm.routing = USAPHMP_ROUTE_DIRECT;
   h->prm.scale = USAPHMP_SCALE_RAW;
+  h->prm.local_search = 0;
   const int r = create_common(h, W, C, dev, static_cast<cudaStream_t>(stream));
   if (r != USAPHMP_OK) {
     const std::string msg = g_err;
@@ -401,6 +404,8 @@ int ensure_ga(usaphmp_s* h) {
     h->rpart_cap = np;
   }
   if (!h->d_dist64) CK(dalloc(&h->d_dist64, (size_t)h->p * h->p));
+  if (!h->d_ls) CK(dalloc(&h->d_ls, local_search_scratch_doubles(h->n, h->p)));
+  if (!h->d_ls_count) CK(dalloc(&h->d_ls_count, 2));
   return USAPHMP_OK;
 }
 
@@ -481,7 +486,7 @@ void usaphmp_destroy(usaphmp_t h) {
   dfree(h->W); dfree(h->C); dfree(h->CTbuf); dfree(h->O); dfree(h->D); dfree(h->Whi); dfree(h->Wlo);
   if (h->tmaps) cudaFree(h->tmaps);
   dfree(h->d_status); dfree(h->d_bad); dfree(h->d_dscratch); dfree(h->d_cost); dfree(h->d_rpart);
-  dfree(h->d_dist64); dfree(h->d_total);
+  dfree(h->d_dist64); dfree(h->d_total); dfree(h->d_ls); dfree(h->d_ls_count);
   if (h->h_status) cudaFreeHost(h->h_status);
   if (h->h_bad) cudaFreeHost(h->h_bad);
   h->ev.release(); h->ga.release(); h->one.release();
@@ -508,6 +513,7 @@ int usaphmp_set_params(usaphmp_t h, const usaphmp_params* prm) {
     return fail(USAPHMP_EINVAL, "unknown scale");
   if (prm->scale == USAPHMP_SCALE_PER_FLOW && !(h->total_flow > 0.0))
     return fail(USAPHMP_EINVAL, "scale per unit flow needs a positive total flow");
+  if (prm->local_search < 0) return fail(USAPHMP_EINVAL, "local_search must be >= 0");
   h->prm = *prm;
   h->ga_ready = false;
   drop_graph(h);
@@ -742,6 +748,23 @@ int usaphmp_select_dev(usaphmp_t h, int32_t R, int32_t P, int32_t g, const uint3
   return USAPHMP_OK;
 }
 
+int usaphmp_local_search_dev(usaphmp_t h, int32_t B, const int32_t* hubs, uint8_t* slot, int32_t max_sweeps,
+                             int32_t* moves, int32_t* sweeps, void* stream) {
+  if (!h || !hubs || !slot) return fail(USAPHMP_EINVAL, "NULL argument");
+  if (B <= 0) return B == 0 ? USAPHMP_OK : fail(USAPHMP_EINVAL, "B < 0");
+  if (max_sweeps < 1) return fail(USAPHMP_EINVAL, "max_sweeps must be >= 1");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double* scratch = nullptr;
+  CK(dalloc(&scratch, (size_t)B * local_search_scratch_doubles(h->n, h->p)));
+  launch_local_search(inst_of(h), B, hubs, slot, max_sweeps, scratch, moves, sweeps, s);
+  cudaError_t e = cudaGetLastError();
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  cudaFree(scratch);
+  CK(e);
+  CK(e2);
+  return USAPHMP_OK;
+}
+
 int usaphmp_rescore_fp64_dev(usaphmp_t h, int32_t B, const int32_t* hubs, const uint8_t* slot, double* cost,
                              void* stream) {
   if (!h || !hubs || !slot || !cost) return fail(USAPHMP_EINVAL, "NULL argument");
@@ -867,6 +890,17 @@ int usaphmp_ga_result(usaphmp_t h, usaphmp_result* best, void* stream) {
   TaskSet ts{nullptr, &t1, 1};
   launch_alloc(ts, true, false, s);
   CK(cudaGetLastError());
+  if (h->prm.local_search > 0) {
+    // improve the nearest allocation of the best hubs, then take the fast
+    // path's fitness of the improved solution
+    launch_local_search(inst_of(h), 1, h->one.hubs, h->one.slot, h->prm.local_search, h->d_ls, h->d_ls_count,
+                        h->d_ls_count + 1, s);
+    CK(cudaGetLastError());
+    PopBuf pb = popbuf(h, h->one, 1);
+    pb.slot_in = h->one.slot;
+    RET(run_eval(h, make_task(h, pb), false, s));
+    CK(cudaMemcpyAsync(&bf, h->one.fit, sizeof(float), cudaMemcpyDeviceToHost, s));
+  }
   launch_rescore(inst_of(h), 1, h->one.hubs, h->one.slot, h->d_rpart, h->d_cost, s, h->d_dist64,
                  output_scale(h));
   CK(cudaGetLastError());

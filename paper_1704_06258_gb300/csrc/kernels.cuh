@@ -117,6 +117,12 @@ void launch_rescore(const DevInst& in, int B, const int32_t* hubs, const uint8_t
                     double* part, double* cost, cudaStream_t s, double* dist = nullptr, double scale = 1.0);
 int rescore_parts(int n);
 
+// local_search.cu: fp64 single-reallocation sweeps for fixed hubs (slots in
+// place); scratch holds local_search_scratch_doubles(n, p) per chromosome.
+size_t local_search_scratch_doubles(int n, int p);
+void launch_local_search(const DevInst& in, int B, const int32_t* hubs, uint8_t* slot, int max_sweeps,
+                         double* scratch, int32_t* moves, int32_t* sweeps, cudaStream_t s);
+
 // capi.cu: records the calling thread's last error message; returns `code`.
 int report_error(int code, const std::string& msg);
 
