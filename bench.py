@@ -319,6 +319,40 @@ def routing_leg(steps, warmup, flush, stream):
     return out
 
 
+def local_search_leg(stream):
+    """Allocation local search (fp64 single reallocations) on 64 random hub
+    sets of the bench instance (clustered n=1000, p=20), from their nearest
+    allocations to a local optimum: wall time of the call, sweeps and moves,
+    and the relative gain of the fp64 objective."""
+    import torch
+    from paper_1704_06258_gb300 import synth
+    from paper_1704_06258_gb300.binding import Instance
+    inst = synth.clustered()
+    B = 64
+    hubs, _ = synth.random_population(123, inst.n, inst.p, B)
+    hs = np.sort(hubs, axis=1).astype(np.int32)
+    with Instance.from_instance(inst) as gi:
+        d_h = torch.from_numpy(hs).cuda()
+        d_s = torch.empty((B, gi.ns), dtype=torch.uint8, device="cuda")
+        gi.allocate_dev(B, d_h.data_ptr(), d_s.data_ptr(), stream)
+        c0 = torch.empty(B, dtype=torch.float64, device="cuda")
+        c1 = torch.empty(B, dtype=torch.float64, device="cuda")
+        gi.rescore_fp64_dev(B, d_h.data_ptr(), d_s.data_ptr(), c0.data_ptr(), stream)
+        mv = torch.zeros(B, dtype=torch.int32, device="cuda")
+        sw = torch.zeros(B, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gi.local_search_dev(B, d_h.data_ptr(), d_s.data_ptr(), 50, mv.data_ptr(), sw.data_ptr(), stream)
+        ms = (time.perf_counter() - t0) * 1e3
+        gi.rescore_fp64_dev(B, d_h.data_ptr(), d_s.data_ptr(), c1.data_ptr(), stream)
+        torch.cuda.synchronize()
+        gain = (c0 - c1) / c0
+        return {"chromosomes": B, "max_sweeps": 50, "call_ms": ms, "mean_sweeps": float(sw.float().mean()),
+                "mean_moves": float(mv.float().mean()), "mean_rel_gain": float(gain.mean()),
+                "max_rel_gain": float(gain.max()), "workload": "clustered n=1000 p=20, random hub sets, "
+                                                            "nearest allocation in, local optimum out"}
+
+
 def factor_sweep():
     """The study of §6.2 (Fig. 3) on a synthetic 25-node instance (the CAB
     data set has 25 cities but is not available): for collection and
@@ -375,6 +409,7 @@ def run_ours(args):
     large = large_n_leg(20, 3, flush, stream) if (not only_split and world == 1 and args.large) else None
     routed = routing_leg(200, 3, flush, stream) if (not only_split and world == 1 and args.large) else None
     sweep = factor_sweep() if (not only_split and world == 1 and args.large) else None
+    lsearch = local_search_leg(stream) if (not only_split and world == 1 and args.large) else None
     if only_split:
         plain = dict(split)
     ms0 = split["generation"]
@@ -427,6 +462,7 @@ def run_ours(args):
         "large_n": large,
         "routing_hub_paths": routed,
         "factor_sweep": sweep,
+        "local_search": lsearch,
         "p50_solve_ms": serving["p50_ms"] if serving else None,
         "p99_solve_ms": serving["p99_ms"] if serving else None,
         "serving": serving,
