@@ -49,43 +49,72 @@ __global__ void __launch_bounds__(256) k_alloc(const __grid_constant__ TaskParam
   __syncthreads();
 
   float acc = 0.f;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    int bl;
-    float cih;  // C[i, h(i)]
-    if (kNearest) {
-      bl = 0;
-      cih = CT[(long long)hs[0] * ldw + i];
-      int own = (hs[0] == i) ? 0 : -1;
+  if (kNearest) {
+    // Four consecutive nodes per thread: one 16-byte load of CT[hub][i..i+3]
+    // per hub (rows are zero-padded to ldw, a multiple of 8), compares in
+    // ascending hub order per node (lowest hub on ties).  Hubs serve
+    // themselves: a node that is a hub takes its own slot afterwards.
+    __shared__ uint32_t hub_bits[kMaxN / 32];
+    for (int w = threadIdx.x; w < (n + 31) / 32; w += blockDim.x) hub_bits[w] = 0u;
+    __syncthreads();
+    for (int k = threadIdx.x; k < p; k += blockDim.x) atomicOr(&hub_bits[hs[k] >> 5], 1u << (hs[k] & 31));
+    __syncthreads();
+    const int n4 = (n + 3) >> 2;
+    for (int g = threadIdx.x; g < n4; g += blockDim.x) {
+      const int i0 = g << 2;
+      float4 best = __ldg(reinterpret_cast<const float4*>(CT + (long long)hs[0] * ldw) + g);
+      int b0 = 0, b1 = 0, b2 = 0, b3 = 0;
       int l = 1;
-      // 8 loads in flight, then the compares in ascending hub order
-      for (; l + 8 <= p; l += 8) {
-        float v[8];
+      for (; l + 4 <= p; l += 4) {
+        float4 v[4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = __ldg(CT + (long long)hs[l + u] * ldw + i);
+        for (int u = 0; u < 4; ++u) v[u] = __ldg(reinterpret_cast<const float4*>(CT + (long long)hs[l + u] * ldw) + g);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          if (v[u] < cih) { cih = v[u]; bl = l + u; }
-          if (hs[l + u] == i) own = l + u;
+        for (int u = 0; u < 4; ++u) {
+          if (v[u].x < best.x) { best.x = v[u].x; b0 = l + u; }
+          if (v[u].y < best.y) { best.y = v[u].y; b1 = l + u; }
+          if (v[u].z < best.z) { best.z = v[u].z; b2 = l + u; }
+          if (v[u].w < best.w) { best.w = v[u].w; b3 = l + u; }
         }
       }
       for (; l < p; ++l) {
-        const int hl = hs[l];
-        const float v = __ldg(CT + (long long)hl * ldw + i);
-        if (v < cih) { cih = v; bl = l; }
-        if (hl == i) own = l;
+        const float4 v = __ldg(reinterpret_cast<const float4*>(CT + (long long)hs[l] * ldw) + g);
+        if (v.x < best.x) { best.x = v.x; b0 = l; }
+        if (v.y < best.y) { best.y = v.y; b1 = l; }
+        if (v.z < best.z) { best.z = v.z; b2 = l; }
+        if (v.w < best.w) { best.w = v.w; b3 = l; }
       }
-      if (own >= 0) { bl = own; cih = CT[(long long)i * ldw + i]; }
-      slot[i] = (uint8_t)bl;
-    } else {
-      bl = slot_in[i];
+      // one node of the group: own slot for a hub, access terms, slot code
+      auto finish = [&](int i, int bl, float cih) -> uint32_t {
+        if (i >= n) return (uint32_t)kSlotPad;
+        if ((hub_bits[i >> 5] >> (i & 31)) & 1u) {
+          for (int q = 0; q < p; ++q)
+            if (hs[q] == i) bl = q;
+          cih = CT[(long long)i * ldw + i];
+        }
+        const float chi_i = sym ? cih : C[(long long)hs[bl] * ldw + i];  // C[h(i), i]
+        acc += access_term(chi, O[i], cih, delta, D[i], chi_i);
+        return (uint32_t)bl;
+      };
+      const uint32_t s0 = finish(i0, b0, best.x);
+      const uint32_t s1 = finish(i0 + 1, b1, best.y);
+      const uint32_t s2 = finish(i0 + 2, b2, best.z);
+      const uint32_t s3 = finish(i0 + 3, b3, best.w);
+      const uint32_t packed = s0 | (s1 << 8) | (s2 << 16) | (s3 << 24);
+      *reinterpret_cast<uint32_t*>(slot + i0) = packed;
+    }
+    for (int i = (n4 << 2) + threadIdx.x; i < ns; i += blockDim.x) slot[i] = kSlotPad;
+  } else {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      int bl = slot_in[i];
       if (bl >= p) { bad = true; bl = 0; }
       slot[i] = (uint8_t)bl;
-      cih = CT[(long long)hs[bl] * ldw + i];
+      const float cih = CT[(long long)hs[bl] * ldw + i];             // C[i, h(i)]
+      const float chi_i = sym ? cih : C[(long long)hs[bl] * ldw + i];  // C[h(i), i]
+      acc += access_term(chi, O[i], cih, delta, D[i], chi_i);
     }
-    const float chi_i = sym ? cih : C[(long long)hs[bl] * ldw + i];  // C[h(i), i]
-    acc += access_term(chi, O[i], cih, delta, D[i], chi_i);
+    for (int i = n + threadIdx.x; i < ns; i += blockDim.x) slot[i] = kSlotPad;
   }
-  for (int i = n + threadIdx.x; i < ns; i += blockDim.x) slot[i] = kSlotPad;
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(T.pop.status, kStatusBadChromosome);
   const float s = block_sum(acc, red);
   if (threadIdx.x == 0) T.pop.t12[b] = s;
