@@ -87,7 +87,9 @@ typedef struct usaphmp_s* usaphmp_t;
 typedef struct {
   int32_t islands;      /* R >= 1 (default 64) */
   int32_t island_size;  /* P, even, >= 2 (default 64); population B = R*P */
-  int32_t n1;           /* generations between island merges (default 10) */
+  int32_t n1;           /* generations between island merges (default 10);
+                           0: never merge (a caller sharding islands over GPUs
+                           merges them with usaphmp_ga_islands / _ga_merge) */
   int32_t path;         /* USAPHMP_PATH_* (default SPLIT_BF16) */
   int32_t elitist;      /* 0 (default): ancestor = best child unconditionally */
   int32_t use_graph;    /* 1 (default): replay generations from a CUDA graph */
@@ -100,6 +102,11 @@ typedef struct {
                            search (usaphmp_local_search_dev) applied to the
                            returned solution; the GA itself evaluates nearest
                            allocations */
+  int32_t island_offset; /* >= 0 (default 0): global index of this handle's
+                            first island.  Random streams are addressed by the
+                            global chromosome index (island_offset + r) * P + j,
+                            so shards of one island population over several
+                            GPUs draw what one GPU holding all islands draws */
 } usaphmp_params;
 
 typedef struct {
@@ -180,6 +187,18 @@ int usaphmp_select_dev(usaphmp_t h, int32_t R, int32_t P, int32_t g, const uint3
                        float* best_fit, void* stream);
 
 /* FP64 objective (pair form of eq. 1) of B canonical chromosomes: cost [B]. */
+/* Island exchange for a population sharded over GPUs (§5 outer loop; the
+ * caller moves the data between processes).  usaphmp_ga_islands copies the
+ * current ancestors (host, [R][nw] words, bit i%32 of word i/32 = node i)
+ * and their fitness (host, [R] raw fp32 costs); either output may be NULL.
+ * usaphmp_ga_merge sets every island's ancestor to `mask` (host, nw words,
+ * exactly p bits among the first n) with fitness `fit`: the merge the GA
+ * does itself every n1 generations when all islands are on one GPU (run
+ * with n1 = 0 and call this after every n1 generations).  Both need
+ * usaphmp_ga_begin first and synchronise `stream`. */
+int usaphmp_ga_islands(usaphmp_t h, uint32_t* masks, float* fit, void* stream);
+int usaphmp_ga_merge(usaphmp_t h, const uint32_t* mask, float fit, void* stream);
+
 /* Allocation local search for fixed hubs, in fp64 (§4.1 allocates every
  * spoke to its nearest hub, which is not always the cheapest allocation for
  * those hubs).  A sweep visits the spokes in ascending node order and moves

@@ -87,24 +87,27 @@ def correct(mask, p, stream):
     return mask
 
 
-def make_children(ancestors, seed, g, p, P):
+def make_children(ancestors, seed, g, p, P, island_offset=0):
     """One generation of offspring: exchange -> crossover -> mutation -> correction.
 
     ancestors: bool [R, n].  Returns bool [R*P, n]; chromosome q = r*P + j
-    belongs to island r.
+    belongs to island r.  The draw streams are addressed by the global index
+    (island_offset*P + q), so a slice of the islands draws what the whole
+    population draws for them.
     """
     R, n = ancestors.shape
     B = R * P
+    q0 = island_offset * P
     parents = np.empty((B, n), dtype=bool)
     for q in range(B):
-        parents[q] = exchange(ancestors[q // P].copy(), DrawStream(seed, g, q, OP_PERTURB))
+        parents[q] = exchange(ancestors[q // P].copy(), DrawStream(seed, g, q0 + q, OP_PERTURB))
     children = parents.copy()
     for q in range(0, B, 2):
-        ca, cb, _ = crossover(parents[q], parents[q + 1], DrawStream(seed, g, q, OP_CROSSOVER))
+        ca, cb, _ = crossover(parents[q], parents[q + 1], DrawStream(seed, g, q0 + q, OP_CROSSOVER))
         children[q], children[q + 1] = ca, cb
     for q in range(B):
-        exchange(children[q], DrawStream(seed, g, q, OP_MUTATION))
-        correct(children[q], p, DrawStream(seed, g, q, OP_CORRECTION))
+        exchange(children[q], DrawStream(seed, g, q0 + q, OP_MUTATION))
+        correct(children[q], p, DrawStream(seed, g, q0 + q, OP_CORRECTION))
     return children
 
 
@@ -134,7 +137,9 @@ def _rank(x):
 
 
 def select(state, children, fitness, g, P, N1, elitist=False):
-    """Inner-loop selection and the outer-loop merge of §5, in place on `state`."""
+    """Inner-loop selection and the outer-loop merge of §5, in place on `state`
+    (N1 = 0: no merge; a population split over several GPUs merges across
+    them instead, see merge_shards)."""
     R = state.ancestors.shape[0]
     fitness = _rank(fitness)
     for r in range(R):
@@ -148,10 +153,29 @@ def select(state, children, fitness, g, P, N1, elitist=False):
     if state.anc_fit[rb] < state.best_fit:
         state.best = state.ancestors[rb].copy()
         state.best_fit = float(state.anc_fit[rb])
-    if (g + 1) % N1 == 0:
+    if N1 > 0 and (g + 1) % N1 == 0:
         state.ancestors[:] = state.ancestors[rb]
         state.anc_fit[:] = state.anc_fit[rb]
     return state
+
+
+def merge_shards(states, island_counts):
+    """The §5 merge across shards of one island population: every island of
+    every shard takes the ancestor of the island with the smallest ancestor
+    fitness over all shards (NaN last; lowest global island index on ties).
+    `states` are the shards' States in global island order."""
+    best = None
+    base = 0
+    for st, R in zip(states, island_counts):
+        f = _rank(st.anc_fit)
+        r = int(np.argmin(f))
+        if best is None or f[r] < best[0]:
+            best = (f[r], st.ancestors[r].copy(), float(st.anc_fit[r]))
+        base += R
+    for st in states:
+        st.ancestors[:] = best[1]
+        st.anc_fit[:] = best[2]
+    return best[1], best[2]
 
 
 def solve(inst, generations, seed, R=1, P=64, N1=10, elitist=False, fitness_fn=None, routing="direct"):

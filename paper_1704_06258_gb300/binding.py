@@ -35,7 +35,7 @@ c_i32, c_i64, c_u64, c_f64, c_f32, c_vp = (ctypes.c_int32, ctypes.c_int64, ctype
 class Params(ctypes.Structure):
     _fields_ = [("islands", c_i32), ("island_size", c_i32), ("n1", c_i32), ("path", c_i32),
                 ("elitist", c_i32), ("use_graph", c_i32), ("routing", c_i32), ("scale", c_i32),
-                ("local_search", c_i32)]
+                ("local_search", c_i32), ("island_offset", c_i32)]
 
 
 class Result(ctypes.Structure):
@@ -84,6 +84,8 @@ _SIGS = {
     "usaphmp_server_poll": (c_i32, [c_vp, c_i64, ctypes.POINTER(Result)]),
     "usaphmp_server_footprint": (c_i32, [c_i32, c_i32, c_i32, c_i32, ctypes.POINTER(c_i64)]),
     "usaphmp_server_destroy": (None, [c_vp]),
+    "usaphmp_ga_islands": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
+    "usaphmp_ga_merge": (c_i32, [c_vp, c_vp, c_f32, c_vp]),
     "usaphmp_local_search_dev": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp]),
     "usaphmp_set_tile": (c_i32, [c_vp, ctypes.POINTER(Tile)]),
     "usaphmp_get_tile": (c_i32, [c_vp, ctypes.POINTER(Tile)]),
@@ -291,6 +293,21 @@ class Instance:
         acc = (c_f64 * 6)()
         check(lib().usaphmp_ga_run_profiled(self.h, generations, stream, acc))
         return dict(zip(STAGES, list(acc)))
+
+    def ga_islands(self, stream=0):
+        """usaphmp_ga_islands: (masks uint32 [R, nw], fitness float32 [R])."""
+        R = self.params["islands"]
+        masks = np.empty((R, self.nw), dtype=np.uint32)
+        fit = np.empty(R, dtype=np.float32)
+        check(lib().usaphmp_ga_islands(self.h, _ptr(masks), _ptr(fit), stream))
+        return masks, fit
+
+    def ga_merge(self, mask, fit, stream=0):
+        """usaphmp_ga_merge: every island's ancestor <- mask (uint32 [nw])."""
+        mask = np.ascontiguousarray(mask, dtype=np.uint32)
+        if mask.shape != (self.nw,):
+            raise ValueError("mask must hold nw words")
+        check(lib().usaphmp_ga_merge(self.h, _ptr(mask), float(fit), stream))
 
     def ga_result(self, stream=0):
         hubs = np.empty(self.p, dtype=np.int32)

@@ -346,6 +346,7 @@ int create_impl(int32_t n, int32_t p, const float* W, const float* C, double chi
   h->prm.routing = USAPHMP_ROUTE_DIRECT;
   h->prm.scale = USAPHMP_SCALE_RAW;
   h->prm.local_search = 0;
+  h->prm.island_offset = 0;
   const int r = create_common(h, W, C, dev, static_cast<cudaStream_t>(stream));
   if (r != USAPHMP_OK) {
     const std::string msg = g_err;
@@ -413,6 +414,7 @@ Task ga_task_of(usaphmp_s* h, unsigned long long seed) {
   const int R = h->prm.islands, P = h->prm.island_size;
   Task t = make_task(h, popbuf(h, h->ga, R * P));
   t.ga.R = R; t.ga.P = P; t.ga.N1 = h->prm.n1; t.ga.elitist = h->prm.elitist;
+  t.ga.island_offset = h->prm.island_offset;
   t.ga.seed = seed;
   t.ga.gen = h->gen; t.ga.anc = h->anc; t.ga.anc_fit = h->anc_fit;
   t.ga.best = h->best; t.ga.best_fit = h->best_fit;
@@ -504,7 +506,10 @@ int usaphmp_set_params(usaphmp_t h, const usaphmp_params* prm) {
   if ((long long)prm->islands * prm->island_size > (1 << 24) ||
       (long long)prm->islands * prm->island_size * h->p >= (1ll << 31))
     return fail(USAPHMP_EINVAL, "population too large");
-  if (prm->n1 < 1) return fail(USAPHMP_EINVAL, "n1 must be >= 1");
+  if (prm->n1 < 0) return fail(USAPHMP_EINVAL, "n1 must be >= 0");
+  if (prm->island_offset < 0 ||
+      ((long long)prm->island_offset + prm->islands) * prm->island_size > 0x7fffffffll)
+    return fail(USAPHMP_EINVAL, "island_offset must be >= 0 and (island_offset + islands) * island_size < 2^31");
   if (prm->path != USAPHMP_PATH_PLAIN_FP32 && prm->path != USAPHMP_PATH_SPLIT_BF16)
     return fail(USAPHMP_EINVAL, "unknown path");
   if (prm->routing != USAPHMP_ROUTE_DIRECT && prm->routing != USAPHMP_ROUTE_HUB_PATHS)
@@ -870,6 +875,37 @@ int usaphmp_ga_run_profiled(usaphmp_t h, int32_t generations, void* stream, doub
     stage_ms[5] += all;
     h->ga_evals += B;
   }
+  return USAPHMP_OK;
+}
+
+int usaphmp_ga_islands(usaphmp_t h, uint32_t* masks, float* fit, void* stream) {
+  if (!h) return fail(USAPHMP_EINVAL, "NULL handle");
+  if (!h->ga_ready) return fail(USAPHMP_EINVAL, "usaphmp_ga_begin first");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int R = h->ga_task.ga.R;
+  if (masks) CK(cudaMemcpyAsync(masks, h->anc, sizeof(uint32_t) * R * h->nw, cudaMemcpyDeviceToHost, s));
+  if (fit) CK(cudaMemcpyAsync(fit, h->anc_fit, sizeof(float) * R, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return USAPHMP_OK;
+}
+
+int usaphmp_ga_merge(usaphmp_t h, const uint32_t* mask, float fit, void* stream) {
+  if (!h || !mask) return fail(USAPHMP_EINVAL, "NULL argument");
+  if (!h->ga_ready) return fail(USAPHMP_EINVAL, "usaphmp_ga_begin first");
+  int bits = 0;
+  for (int x = 0; x < h->nw; ++x) {
+    uint32_t v = mask[x];
+    if (x == h->nw - 1 && (h->n & 31)) {
+      if (v >> (h->n & 31)) return fail(USAPHMP_EINVAL, "usaphmp_ga_merge: mask has bits at nodes >= n");
+    }
+    bits += __builtin_popcount(v);
+  }
+  if (bits != h->p) return fail(USAPHMP_EINVAL, "usaphmp_ga_merge: mask does not hold p hubs");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(cudaMemcpyAsync(h->mask0, mask, sizeof(uint32_t) * h->nw, cudaMemcpyHostToDevice, s));
+  launch_set_ancestors(h->anc, h->anc_fit, h->ga_task.ga.R, h->nw, h->mask0, fit, s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
   return USAPHMP_OK;
 }
 

@@ -89,7 +89,8 @@ struct PopBuf {
 
 // Island GA state (§5): R islands of P chromosomes.
 struct GaState {
-  int R, P, N1, elitist;
+  int R, P, N1, elitist;  // N1 = 0: no merge (the caller merges islands across GPUs)
+  int island_offset;      // global index of island 0 (random streams of a shard)
   unsigned long long seed;
   int* gen;            // device generation counter
   uint32_t* anc;       // [R][nw]

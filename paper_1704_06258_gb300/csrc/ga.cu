@@ -145,6 +145,8 @@ __global__ void __launch_bounds__(64) k_children(const __grid_constant__ TaskPar
   const int q0 = 2 * (blockIdx.x - tp.bo.o[t]);
   const int q = q0 + w;
   const int r = q / P;
+  // random streams are addressed by the global chromosome index
+  const uint32_t goff = (uint32_t)T.ga.island_offset * (uint32_t)P;
   uint32_t* par = msm + w * nw;
   uint32_t* oth = msm + (1 - w) * nw;
   uint32_t* ch = msm + (2 + w) * nw;
@@ -156,12 +158,12 @@ __global__ void __launch_bounds__(64) k_children(const __grid_constant__ TaskPar
   }
   __syncwarp();
   {
-    Draws d(seed, g, (uint32_t)q, kOpExchange);
+    Draws d(seed, g, goff + (uint32_t)q, kOpExchange);
     exchange(par, nw, n, d);
   }
   __syncthreads();
   {
-    Draws d(seed, g, (uint32_t)q0, kOpCrossover);
+    Draws d(seed, g, goff + (uint32_t)q0, kOpCrossover);
     const int c = 1 + (int)d.below((uint32_t)(n - 1));
     for (int x = lane; x < nw; x += 32) {
       const uint32_t own = par[x], other = oth[x];
@@ -178,11 +180,11 @@ __global__ void __launch_bounds__(64) k_children(const __grid_constant__ TaskPar
     __syncwarp();
   }
   {
-    Draws d(seed, g, (uint32_t)q, kOpMutation);
+    Draws d(seed, g, goff + (uint32_t)q, kOpMutation);
     exchange(ch, nw, n, d);
   }
   {
-    Draws d(seed, g, (uint32_t)q, kOpCorrection);
+    Draws d(seed, g, goff + (uint32_t)q, kOpCorrection);
     correct(ch, nw, n, p, d);
   }
   uint32_t* out = T.pop.mask + (long long)q * nw;
@@ -275,7 +277,7 @@ __global__ void k_select_global(const __grid_constant__ TaskParam tp) {
     if (threadIdx.x == 0) *T.ga.best_fit = fb;
   }
   const int g = *T.ga.gen;
-  if ((g + 1) % T.ga.N1 == 0) {
+  if (T.ga.N1 > 0 && (g + 1) % T.ga.N1 == 0) {
     for (long long e = threadIdx.x; e < (long long)R * nw; e += blockDim.x) {
       const int r = (int)(e / nw);
       if (r != rb) T.ga.anc[e] = src[e - (long long)r * nw];
@@ -375,7 +377,7 @@ __global__ void __launch_bounds__(128) k_reduce_select(const __grid_constant__ T
     if (threadIdx.x == 0) *T.ga.best_fit = fb;
   }
   const int g = *T.ga.gen;
-  if ((g + 1) % T.ga.N1 == 0) {
+  if (T.ga.N1 > 0 && (g + 1) % T.ga.N1 == 0) {
     for (long long e = threadIdx.x; e < (long long)R * nw; e += blockDim.x) {
       const int rr = (int)(e / nw);
       if (rr != rb) T.ga.anc[e] = __ldcg(src + (e - (long long)rr * nw));
@@ -436,6 +438,19 @@ void launch_select(const TaskSet& ts, cudaStream_t s) {
 
 void launch_ga_init(const Task& task, const uint32_t* mask0, const float* fit0, cudaStream_t s) {
   k_ga_init<<<8, 256, 0, s>>>(task, mask0, fit0);
+}
+
+// Every island's ancestor <- mask (nw words), its fitness <- fit: the merge
+// step of §5 when the best island lives on another GPU.
+__global__ void k_set_ancestors(uint32_t* anc, float* anc_fit, int R, int nw, const uint32_t* mask, float fit) {
+  const int r = blockIdx.x;
+  for (int x = threadIdx.x; x < nw; x += blockDim.x) anc[(long long)r * nw + x] = mask[x];
+  if (threadIdx.x == 0) anc_fit[r] = fit;
+}
+
+void launch_set_ancestors(uint32_t* anc, float* anc_fit, int R, int nw, const uint32_t* mask, float fit,
+                          cudaStream_t s) {
+  if (R > 0) k_set_ancestors<<<R, 128, 0, s>>>(anc, anc_fit, R, nw, mask, fit);
 }
 
 }  // namespace usaphmp

@@ -103,6 +103,8 @@ void launch_reduce(const TaskSet& ts, cudaStream_t s);
 
 // ga.cu: offspring (exchange, crossover, mutation, correction) and selection.
 void launch_children(const TaskSet& ts, cudaStream_t s);
+void launch_set_ancestors(uint32_t* anc, float* anc_fit, int R, int nw, const uint32_t* mask, float fit,
+                          cudaStream_t s);
 void launch_select(const TaskSet& ts, cudaStream_t s);
 // ga.cu: fitness reduction fused with selection (GA generations only).
 void launch_reduce_select(const TaskSet& ts, cudaStream_t s);

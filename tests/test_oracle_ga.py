@@ -152,3 +152,34 @@ def test_ga_reaches_best_nearest_solution_on_tiny_instance():
     hubs, h, c, _ = ga.solve(inst, generations=100, seed=2024, R=1, P=64, N1=10)
     assert c >= bf["opt"][0] * (1 - 1e-12)
     assert c == pytest.approx(bf["nearest"][0], rel=1e-12)
+
+
+def test_sharded_islands_make_the_single_population_decisions():
+    """Two shards of two islands each, drawing by global chromosome index and
+    merged across shards every N1 generations, follow the run of one
+    population of four islands exactly."""
+    inst = synth.urand200(seed=53, n=30, p=4)
+    seed, P, N1, G = 77, 8, 3, 10
+
+    def fitness(children):
+        _, h, _ = ga.allocate_all(inst.C, children)
+        return np.array([cost.pair_cost(inst.W, inst.C, inst.chi, inst.alpha, inst.delta, x) for x in h])
+
+    hubs0, h0 = cost.initial_solution(inst.C, inst.p)
+    mask0 = np.zeros(inst.n, dtype=bool)
+    mask0[hubs0] = True
+    f0 = cost.pair_cost(inst.W, inst.C, inst.chi, inst.alpha, inst.delta, h0)
+    whole = ga.State(np.tile(mask0, (4, 1)), np.full(4, f0), mask0, f0)
+    shards = [ga.State(np.tile(mask0, (2, 1)), np.full(2, f0), mask0, f0) for _ in range(2)]
+    for g in range(G):
+        children = ga.make_children(whole.ancestors, seed, g, inst.p, P)
+        ga.select(whole, children, fitness(children), g, P, N1)
+        for k, st in enumerate(shards):
+            ch = ga.make_children(st.ancestors, seed, g, inst.p, P, island_offset=2 * k)
+            np.testing.assert_array_equal(ch, children[16 * k:16 * (k + 1)])
+            ga.select(st, ch, fitness(ch), g, P, 0)
+        if (g + 1) % N1 == 0:
+            ga.merge_shards(shards, [2, 2])
+        np.testing.assert_array_equal(np.concatenate([s.ancestors for s in shards]), whole.ancestors)
+        np.testing.assert_array_equal(np.concatenate([s.anc_fit for s in shards]), whole.anc_fit)
+    assert min(s.best_fit for s in shards) == whole.best_fit
