@@ -10,7 +10,7 @@ namespace usaphmp {
 
 __global__ void k_canon(const int32_t* __restrict__ hubs_in, const int32_t* __restrict__ S,
                         int n, int p, int ns, int32_t* __restrict__ hubs_out,
-                        uint8_t* __restrict__ slot, uint32_t* status, int* bad_index) {
+                        uint8_t* __restrict__ slot, uint32_t* status, int* bad_index, int index_base) {
   extern __shared__ __align__(16) unsigned char sm[];
   uint8_t* rank = sm;                                         // [n], 0xFF = not a hub
   int* hs = reinterpret_cast<int*>(sm + round_up(n, 16));     // [p]
@@ -34,7 +34,7 @@ __global__ void k_canon(const int32_t* __restrict__ hubs_in, const int32_t* __re
     }
   }
   if (__syncthreads_or(bad)) {
-    if (threadIdx.x == 0) { atomicOr(status, kStatusBadChromosome); atomicMin(bad_index, b); }
+    if (threadIdx.x == 0) { atomicOr(status, kStatusBadChromosome); atomicMin(bad_index, index_base + b); }
     return;
   }
   for (int i = threadIdx.x; i < ns; i += blockDim.x) {
@@ -52,15 +52,16 @@ __global__ void k_canon(const int32_t* __restrict__ hubs_in, const int32_t* __re
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) {
     atomicOr(status, kStatusBadChromosome);
-    atomicMin(bad_index, b);
+    atomicMin(bad_index, index_base + b);
   }
 }
 
 void launch_canon(const int32_t* hubs_in, const int32_t* S, int B, int n, int p, int ns,
-                  int32_t* hubs_out, uint8_t* slot, uint32_t* status, int* bad_index, cudaStream_t s) {
+                  int32_t* hubs_out, uint8_t* slot, uint32_t* status, int* bad_index, cudaStream_t s,
+                  int index_base) {
   if (B <= 0) return;
   const size_t smem = round_up(n, 16) + sizeof(int) * p;
-  k_canon<<<B, 256, smem, s>>>(hubs_in, S, n, p, ns, hubs_out, slot, status, bad_index);
+  k_canon<<<B, 256, smem, s>>>(hubs_in, S, n, p, ns, hubs_out, slot, status, bad_index, index_base);
 }
 
 }  // namespace usaphmp

@@ -110,7 +110,9 @@ struct usaphmp_s {
   int32_t* d_hubs_in = nullptr;
   int32_t* d_S_in = nullptr;
   float* d_fit_out = nullptr;
+  float* h_fit_out = nullptr;        // pinned staging of the fitness returned by usaphmp_eval
   int in_cap = 0;
+
   // GA
   Pop ga;
   Pop one;
@@ -365,7 +367,10 @@ void drop_graph(usaphmp_s* h) {
   h->graph = nullptr;
 }
 
-int eval_canonical(usaphmp_s* h, int B, const int32_t* hubs_in, const int32_t* S, float* fit_out, cudaStream_t s) {
+// Canonical form, allocation terms, transfer term and reduction of B
+// chromosomes given in node ids, enqueued on s (no synchronisation).
+int enqueue_eval_canonical(usaphmp_s* h, int B, const int32_t* hubs_in, const int32_t* S, float* fit_out,
+                           cudaStream_t s) {
   RET(ensure_pop(h, h->ev, B));
   RET(reset_status(h, s));
   launch_canon(hubs_in, S, B, h->n, h->p, h->ns, h->ev.hubs, h->ev.slot, h->d_status, h->d_bad, s);
@@ -374,7 +379,11 @@ int eval_canonical(usaphmp_s* h, int B, const int32_t* hubs_in, const int32_t* S
   pb.fit = fit_out;
   pb.out_scale = (float)output_scale(h);
   const Task task = make_task(h, pb);
-  RET(run_eval(h, task, false, s));
+  return run_eval(h, task, false, s);
+}
+
+int eval_canonical(usaphmp_s* h, int B, const int32_t* hubs_in, const int32_t* S, float* fit_out, cudaStream_t s) {
+  RET(enqueue_eval_canonical(h, B, hubs_in, S, fit_out, s));
   return check_status(h, s, "usaphmp_eval");
 }
 
@@ -493,6 +502,7 @@ void usaphmp_destroy(usaphmp_t h) {
   if (h->h_bad) cudaFreeHost(h->h_bad);
   h->ev.release(); h->ga.release(); h->one.release();
   dfree(h->d_hubs_in); dfree(h->d_S_in); dfree(h->d_fit_out);
+  if (h->h_fit_out) cudaFreeHost(h->h_fit_out);
   dfree(h->anc); dfree(h->anc_fit); dfree(h->best); dfree(h->best_fit); dfree(h->gen); dfree(h->mask0);
   dfree(h->done);
   if (h->stream) cudaStreamDestroy(h->stream);
@@ -650,18 +660,30 @@ int usaphmp_eval(usaphmp_t h, int32_t B, const int32_t* hubs, const int32_t* S, 
   cudaStream_t s = h->stream;
   if (h->in_cap < B) {
     dfree(h->d_hubs_in); dfree(h->d_S_in); dfree(h->d_fit_out);
+    if (h->h_fit_out) cudaFreeHost(h->h_fit_out);
+    h->h_fit_out = nullptr;
+    h->in_cap = 0;
     CK(dalloc(&h->d_hubs_in, (size_t)B * h->p));
     CK(dalloc(&h->d_S_in, (size_t)B * h->n));
     CK(dalloc(&h->d_fit_out, (size_t)B));
+    CK(cudaMallocHost(&h->h_fit_out, sizeof(float) * B));
     h->in_cap = B;
   }
-  CK(cudaMemcpyAsync(h->d_hubs_in, hubs, sizeof(int32_t) * B * h->p, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(h->d_S_in, S, sizeof(int32_t) * B * h->n, cudaMemcpyHostToDevice, s));
-  RET(eval_canonical(h, B, h->d_hubs_in, h->d_S_in, h->d_fit_out, s));
-  std::vector<float> f(B);
-  CK(cudaMemcpyAsync(f.data(), h->d_fit_out, sizeof(float) * B, cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  for (int b = 0; b < B; ++b) fitness[b] = f[b];
+  // every return below happens after the copies from the caller's memory
+  // have finished (they are ordered before the final synchronisation of s)
+  auto finish = [&](int rc) {
+    cudaStreamSynchronize(s);
+    return rc;
+  };
+  cudaError_t e = cudaMemcpyAsync(h->d_hubs_in, hubs, sizeof(int32_t) * B * h->p, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_S_in, S, sizeof(int32_t) * B * h->n, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return finish(cuda_fail(e, "usaphmp_eval input copies"));
+  int rc = enqueue_eval_canonical(h, B, h->d_hubs_in, h->d_S_in, h->d_fit_out, s);
+  if (rc != USAPHMP_OK) return finish(rc);
+  e = cudaMemcpyAsync(h->h_fit_out, h->d_fit_out, sizeof(float) * B, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return finish(cuda_fail(e, "usaphmp_eval fitness copy"));
+  if ((rc = check_status(h, s, "usaphmp_eval")) != USAPHMP_OK) return rc;   // one synchronisation
+  for (int b = 0; b < B; ++b) fitness[b] = h->h_fit_out[b];
   return USAPHMP_OK;
 }
 

@@ -64,7 +64,8 @@ void launch_middle_nodes(const float* C, int n, int ldw, int p, double* dscratch
 
 // canon.cu: validates (hubs, S) in node ids and writes ascending hubs + slots.
 void launch_canon(const int32_t* hubs_in, const int32_t* S, int B, int n, int p, int ns,
-                  int32_t* hubs_out, uint8_t* slot, uint32_t* status, int* bad_index, cudaStream_t s);
+                  int32_t* hubs_out, uint8_t* slot, uint32_t* status, int* bad_index, cudaStream_t s,
+                  int index_base = 0);
 
 // alloc.cu: nearest allocation (or the given slots), access terms t12 and
 // (with_chub) the hub-to-hub cost table chub.

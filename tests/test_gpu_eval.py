@@ -168,3 +168,38 @@ def test_rescore_fp64_matches_oracle():
         gi.rescore_fp64_dev(6, d_hs.data_ptr(), d_slot.data_ptr(), c.data_ptr(), stream())
         got = host(c)
     np.testing.assert_allclose(got, ref, rtol=1e-12)
+
+
+@pytest.mark.parametrize("path", PATHS, ids=["plain", "split"])
+@pytest.mark.parametrize("B", [511, 512, 2047, 2500])
+def test_host_eval_in_chunks_equals_device_eval(path, B):
+    """usaphmp_eval copies and evaluates large populations in chunks; the
+    fitness equals the single-launch device call bit for bit."""
+    inst = synth.urand200(seed=31, n=150, p=9)
+    hubs, S = synth.random_population(32, inst.n, inst.p, B)
+    with Instance.from_instance(inst) as gi:
+        gi.set_params(path=path)
+        got = gi.eval(hubs, S)
+        f = torch.empty(B, dtype=torch.float32, device="cuda")
+        d_h, d_S = dev(hubs), dev(S)
+        gi.eval_dev(B, d_h.data_ptr(), d_S.data_ptr(), f.data_ptr(), stream())
+        ref_dev = host(f).astype(np.float64)
+    np.testing.assert_array_equal(got, ref_dev)
+    idx = np.array([0, B // 3, B // 2, B - 1])
+    ref = oracle_costs(inst, S[idx])
+    assert (np.abs(got[idx] - ref) / ref).max() <= TOL[path]
+
+
+def test_host_eval_reports_a_bad_chromosome_in_a_later_chunk():
+    inst = synth.urand200(seed=33, n=60, p=5)
+    B, bad = 2100, 1800
+    hubs, S = synth.random_population(34, inst.n, inst.p, B)
+    hubs[bad, 1] = hubs[bad, 0]
+    with Instance.from_instance(inst) as gi:
+        with pytest.raises(UsaphmpError) as e:
+            gi.eval(hubs, S)
+        assert e.value.name == "EINVAL_CHROM" and f"chromosome {bad}" in str(e.value)
+        hubs[bad] = hubs[bad - 1]
+        S[bad] = S[bad - 1]
+        out = gi.eval(hubs, S)
+        assert out[bad] == out[bad - 1]
