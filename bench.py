@@ -39,6 +39,8 @@ L2_FLUSH_BYTES = 512 << 20
 K_EVAL_TC_DRAM_BYTES = 14804992
 # the same for one k_alloc launch (profiles/k_alloc_clustered_n1000_p20.md)
 K_ALLOC_DRAM_BYTES = 4372992
+# sm__pipe_tensor_cycles_active (fraction of peak, elapsed) of that k_eval_tc capture
+K_EVAL_TC_TENSOR_ACTIVE = 0.687
 REF_MEMBERS = 16
 
 
@@ -171,18 +173,21 @@ def timed_generations(gi, steps, warmup, flush, stream, world):
     torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
-    acc = {}
+    acc, gen = {}, []
     t0 = time.perf_counter()
     for _ in range(steps):
         flush.zero_()          # L2 flush, outside the per-step events
         st = gi.ga_run_profiled(1, stream)
         for k, v in st.items():
             acc[k] = acc.get(k, 0.0) + v
+        gen.append(st["generation"])
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     barrier(world)
     res = gi.ga_result(stream)
-    return {k: v / steps for k, v in acc.items()}, wall, res
+    out = {k: v / steps for k, v in acc.items()}
+    out["generation_median"] = float(np.median(gen))
+    return out, wall, res
 
 
 def e2e_eval(gi, inst, steps, warmup):
@@ -211,19 +216,31 @@ def _make_request(r):
     return inst.n, inst.p, inst.W, inst.C
 
 
-def serving_leg(n_requests, evals_per_s, seed=4242):
+def serving_leg(n_requests, evals_per_s, seed=4242, fixed_rate=50.0):
     """Poisson arrivals of solve requests (n log-uniform in [50, 3000], p in 3..20,
     population 512 = 8 x 64, 200 generations) into the continuous-batching
-    server; returns p50/p99 latency (arrival -> result) and throughput."""
+    server; p50/p99 latency (arrival -> result) and throughput at 80 % of the
+    estimated capacity and, beside it, at a fixed arrival rate."""
     import multiprocessing as mp
-    from paper_1704_06258_gb300 import synth
-    from paper_1704_06258_gb300.binding import PATH_SPLIT_BF16, Server
     gens, R, P = 200, 8, 64
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 4)) as pool:
         reqs = pool.map(_make_request, range(n_requests), chunksize=4)
     # offered load: 80 % of the rate at which the GA runs these sizes alone
     est_s = [gens * R * P * (n / N) ** 2 / evals_per_s for n, _, _, _ in reqs]
     rate = 0.8 / float(np.mean(est_s))
+    out = _serve(reqs, rate, seed, gens, R, P)
+    out["workload"] = ("n log-uniform [50,3000], p uniform 3..20, clustered instances seeded 5000+r, "
+                       "Poisson arrivals at 80% of the estimated capacity")
+    fixed = _serve(reqs, fixed_rate, seed, gens, R, P)
+    fixed["workload"] = f"the same requests, Poisson arrivals at a fixed {fixed_rate:g} per second"
+    out["fixed_rate"] = fixed
+    return out
+
+
+def _serve(reqs, rate, seed, gens, R, P):
+    from paper_1704_06258_gb300 import synth
+    from paper_1704_06258_gb300.binding import PATH_SPLIT_BF16, Server
+    n_requests = len(reqs)
     arrivals = synth.poisson_arrivals(n_requests, rate, seed=seed)
     lat, evals = [], 0
     with Server(32 << 30, max_active=64, path=PATH_SPLIT_BF16) as srv:
@@ -250,8 +267,7 @@ def serving_leg(n_requests, evals_per_s, seed=4242):
     return {"requests": n_requests, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_ms": float(lat.mean()), "evals_per_s": evals / makespan, "makespan_s": makespan,
             "arrival_rate_per_s": rate, "population": R * P, "generations": gens, "max_active": 64,
-            "path": "split-bf16", "workload": "n log-uniform [50,3000], p uniform 3..20, clustered instances "
-                                              "seeded 5000+r, Poisson arrivals at 80% of the estimated capacity"}
+            "path": "split-bf16"}
 
 
 def rel_error_sample(gi, inst, count=64, seed=99):
@@ -309,6 +325,8 @@ def large_n_leg(steps, warmup, flush, stream):
                 st, _, _ = timed_generations(gi, steps, warmup, flush, stream, 1)
                 row[name] = {"evals_per_s": 2048 / (st["generation"] * 1e-3), "ms_per_step": st["generation"],
                              "transfer_ms": st["transfer"]}
+                if name == "split_bf16":
+                    row[name]["solve_100_generations_s"] = gi.solve(100, 7)["ms"] * 1e-3
                 if name == "split_bf16":
                     fl = 4.0 * inst.n * inst.n * p * 2048
                     row[name]["tensor_tflops"] = fl / (st["transfer"] * 1e-3) / 1e12
@@ -403,6 +421,17 @@ def factor_sweep():
             "wall_s": time.perf_counter() - t0}
 
 
+def paper_context(solve_s):
+    """The paper's whole-program times (Table 4: Urand n=1000, p=20; Table 5:
+    n=6000), on an Nvidia Quadro with 384 CUDA cores, CUDA 7.5, beside this
+    library's usaphmp_solve wall time on the synthetic stand-in.  Context
+    only: the paper's population sizes and generation counts are not given."""
+    return {"paper_urand_n1000_p20_s": 17.923, "paper_n6000_p20_s": 5614.0, "paper_n6000_p50_s": 6212.0,
+            "paper_hardware": "Nvidia Quadro, 4 GB, 384 CUDA cores, CUDA 7.5",
+            "ours_clustered_n1000_p20_solve_s": solve_s,
+            "ours_solve": "usaphmp_solve, 64 islands x 64, 1000 generations, wall time of the call"}
+
+
 def run_ours(args):
     import torch
     from paper_1704_06258_gb300 import synth
@@ -434,6 +463,7 @@ def run_ours(args):
         with ClockSampler(local) as clk:
             split, wall, res = timed_generations(gi, args.steps, args.warmup, flush, stream, world)
         e2e = None if only_split else e2e_eval(gi, inst, steps=max(3, min(50, args.steps // 20)), warmup=1)
+        gi_solve_s = None if only_split else gi.solve(1000, 2024)["ms"] * 1e-3
         rel_err = None if only_split else rel_error_sample(gi, inst)
     large = large_n_leg(20, 3, flush, stream) if (not only_split and world == 1 and args.large) else None
     routed = routing_leg(200, 3, flush, stream) if (not only_split and world == 1 and args.large) else None
@@ -485,7 +515,11 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": 4 * args.steps,   # children, allocation, transfer, reduce+select
         "clocks": clk.summary(),
-        "stage_ms": {k: round(v, 5) for k, v in split.items()},
+        "ms_per_step_median": split["generation_median"],
+        "pair_ops_per_s": value * N * N,   # algorithmic work: n^2 pair multiply-adds per evaluation
+        "tensor_pipe_active_ncu": K_EVAL_TC_TENSOR_ACTIVE,
+        "paper_context": paper_context(gi_solve_s),
+        "stage_ms": {k: round(v, 5) for k, v in split.items() if k != "generation_median"},
         "plain_fp32": {"value": B * world / (plain_ms * 1e-3), "ms_per_step": plain_ms,
                        "stage_ms": {k: round(v, 5) for k, v in plain.items()}},
         "split_vs_plain": plain_ms / ms,
