@@ -21,10 +21,15 @@ namespace {
 // Hub-path tables up to this many entries (p <= 110) are relaxed in shared
 // memory; larger ones in place in global memory.
 constexpr int kFwSmemEntries = 12288;
+// Threads per chromosome block: with four nodes per thread, 128 threads keep
+// a block of n = 1000 nodes two groups deep and let more blocks share an SM.
+constexpr int kAllocThreads = 128;
+// Hub-path table entries each thread keeps in registers (p*p <= kFwOwn * kAllocThreads).
+constexpr int kFwOwn = 4;
 }
 
 template <bool kNearest>
-__global__ void __launch_bounds__(256) k_alloc(const __grid_constant__ TaskParam tp, int with_chub) {
+__global__ void __launch_bounds__(kAllocThreads) k_alloc(const __grid_constant__ TaskParam tp, int with_chub) {
   __shared__ int hs[kMaxP];
   __shared__ float red[32];
   const int t = task_of(tp.bo, blockIdx.x);
@@ -133,29 +138,29 @@ __global__ void __launch_bounds__(256) k_alloc(const __grid_constant__ TaskParam
       extern __shared__ float fw[];
       const bool in_smem = p * p <= kFwSmemEntries;
       __syncthreads();
-      if (in_smem && p * p <= 4 * 256 && blockDim.x == 256) {
-        // p <= 32: every thread owns up to 4 entries and keeps them in
+      if (in_smem && p * p <= kFwOwn * kAllocThreads) {
+        // small p: every thread owns up to kFwOwn entries and keeps them in
         // registers; shared memory holds the table for the others' reads.
-        float v[4];
-        int e4[4];
+        float v[kFwOwn];
+        int e4[kFwOwn];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int e = threadIdx.x + 256 * k;
+        for (int k = 0; k < kFwOwn; ++k) {
+          const int e = threadIdx.x + kAllocThreads * k;
           const int a = e / p, c = e - a * p;
           e4[k] = e < p * p ? e : -1;
           v[k] = e < p * p ? ch[a * hst + c] : 0.f;
           if (e < p * p) fw[e] = v[k];
         }
         __syncthreads();
-        int ra[4], rc[4];
+        int ra[kFwOwn], rc[kFwOwn];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < kFwOwn; ++k) {
           ra[k] = e4[k] >= 0 ? e4[k] / p : 0;
           rc[k] = e4[k] >= 0 ? e4[k] - ra[k] * p : 0;
         }
         for (int m = 0; m < p; ++m) {
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
+          for (int k = 0; k < kFwOwn; ++k) {
             if (e4[k] >= 0) {
               const float nv = fw[ra[k] * p + m] + fw[m * p + rc[k]];
               if (nv < v[k]) {
@@ -167,7 +172,7 @@ __global__ void __launch_bounds__(256) k_alloc(const __grid_constant__ TaskParam
           __syncthreads();
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < kFwOwn; ++k)
           if (e4[k] >= 0) ch[ra[k] * hst + rc[k]] = v[k];
       } else {
         // warp w relaxes rows w, w + nwarps, ...; lane l columns l, l + 32, ...
@@ -208,9 +213,9 @@ void launch_alloc(const TaskSet& ts, bool nearest, bool with_chub, cudaStream_t 
     if (ts.h[t].in.routing && p * p <= kFwSmemEntries) smem = std::max(smem, (size_t)p * p * sizeof(float));
   }
   if (nearest)
-    k_alloc<true><<<blocks, 256, smem, s>>>(tp, with_chub ? 1 : 0);
+    k_alloc<true><<<blocks, kAllocThreads, smem, s>>>(tp, with_chub ? 1 : 0);
   else
-    k_alloc<false><<<blocks, 256, smem, s>>>(tp, with_chub ? 1 : 0);
+    k_alloc<false><<<blocks, kAllocThreads, smem, s>>>(tp, with_chub ? 1 : 0);
 }
 
 }  // namespace usaphmp
