@@ -122,6 +122,22 @@ __device__ inline float warp_sum(float v) {
   return v;
 }
 
+// sum_{r < rows} x[r * stride], added in ascending r (the fixed order every
+// evaluator's partial sums are reduced in), loads issued eight at a time.
+__device__ __forceinline__ float sum_rows_in_order(const float* __restrict__ x, int rows, long long stride) {
+  float s = 0.f;
+  int r = 0;
+  for (; r + 8 <= rows; r += 8) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = x[(long long)(r + u) * stride];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s += v[u];
+  }
+  for (; r < rows; ++r) s += x[(long long)r * stride];
+  return s;
+}
+
 // Block-wide sum in a fixed order (warp butterflies, then warps in order).
 // `red` holds at least blockDim.x/32 floats. Result valid in every thread.
 __device__ inline float block_sum(float v, float* red) {

@@ -308,9 +308,7 @@ __global__ void __launch_bounds__(128) k_reduce_select(const __grid_constant__ T
   int idx = 0x7fffffff;
   for (int j = threadIdx.x; j < P; j += blockDim.x) {
     const int q = r * P + j;
-    const float* __restrict__ part = T.pop.part + q;
-    float s = 0.f;
-    for (int rr = 0; rr < T.pop.npart; ++rr) s += part[(long long)rr * B];
+    const float s = sum_rows_in_order(T.pop.part + q, T.pop.npart, B);
     const float f = T.pop.t12[q] + T.in.alpha * s;
     T.pop.fit[q] = f;
     const float x = rank_key(f);

@@ -14,9 +14,7 @@ __global__ void k_reduce(const __grid_constant__ TaskParam tp) {
   const int b = (blockIdx.x - tp.bo.o[t]) * blockDim.x + threadIdx.x;
   const int B = T.pop.B;
   if (b >= B) return;
-  const float* __restrict__ part = T.pop.part + b;
-  float s = 0.f;
-  for (int r = 0; r < T.pop.npart; ++r) s += part[(long long)r * B];
+  const float s = sum_rows_in_order(T.pop.part + b, T.pop.npart, B);
   T.pop.fit[b] = (T.pop.t12[b] + T.in.alpha * s) * T.pop.out_scale;
 }
 
