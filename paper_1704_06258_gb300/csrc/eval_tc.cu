@@ -12,9 +12,9 @@
 //   * the one-hot operand is never stored in global memory: producer warps
 //     expand it from the u8 slot codes straight into shared memory, in the
 //     same swizzled K-major layout;
-//   * a column tile holds whole chromosomes only (CPT = floor(256/p) of them,
-//     MMA width N = CPT*p rounded up to 16), so the epilogue can finish each
-//     chromosome inside the tile: every thread (one row i of W) forms
+//   * a column tile holds whole chromosomes only (CPT = floor(ntile/p) of
+//     them, MMA width N = CPT*p rounded up to 16), so the epilogue can finish
+//     each chromosome inside the tile: every thread (one row i of W) forms
 //     sum_l D[i][(b,l)] * Chub_b[s_b(i)][l] with the Chub tables of the
 //     tile's chromosomes bulk-copied into shared memory, and a warp
 //     butterfly adds the 32 rows; one partial per (32-row group, chromosome)
@@ -22,11 +22,12 @@
 // Persistent kernel, one CTA per SM, warp roles: 0 TMA, 1 MMA (+ TMEM
 // allocation), 2-9 epilogue (warp w reads TMEM lane quarter w%4 and one half
 // of the tile's chromosomes), 10-17 one-hot producers.  Tiles are 128 rows x
-// N columns x 64-deep K blocks, three
-// shared-memory stages, two TMEM accumulators (2 x 256 columns) so the
-// epilogue of one tile overlaps the MMAs of the next.  Every wait is bounded:
-// after kTimeoutNs the kernel raises kStatusTimeout, drains its own copies
-// and MMAs, frees TMEM and returns.
+// N columns x 64-deep K blocks; the tile shape of a launch (TcTile: ntile
+// 64/128/256, 2-4 shared-memory stages, raster order) sets the layout of
+// shared memory, and two TMEM accumulators of ntile columns let the epilogue
+// of one tile overlap the MMAs of the next.  Every wait is bounded: after
+// kTimeoutNs the kernel raises kStatusTimeout, drains its own copies and
+// MMAs, frees TMEM and returns.
 #include "common.cuh"
 #include "kernels.cuh"
 #include "tc_ptx.cuh"
