@@ -70,6 +70,15 @@ __device__ __forceinline__ float plain_global_sum(const float* __restrict__ W, c
   return acc;
 }
 
+// The KB slot codes of one node (node-major layout, KB-byte aligned).
+template <int KB>
+__device__ __forceinline__ unsigned long long node_codes(const uint8_t* q) {
+  if constexpr (KB == 8) return *reinterpret_cast<const unsigned long long*>(q);
+  else if constexpr (KB == 4) return *reinterpret_cast<const uint32_t*>(q);
+  else if constexpr (KB == 2) return *reinterpret_cast<const uint16_t*>(q);
+  else return *q;
+}
+
 }  // namespace
 
 template <int KB>
@@ -104,13 +113,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_plain(const __grid_constan
     }
     tab[e] = v;
   }
+  // slot codes node-major: sl[j * KB + bb], the KB codes of one node in one
+  // KB-byte word (one shared load per row for all chromosomes of the block)
   {
-    const int vec = ns / 16;  // ns is a multiple of 64
-    const uint4* src = reinterpret_cast<const uint4*>(T.pop.slot + (long long)b0 * ns);
-    uint4* dst = reinterpret_cast<uint4*>(sl);
-    for (int e = threadIdx.x; e < KB * vec; e += kThreads) {
-      const int bb = e / vec;
-      dst[e] = (bb < nb) ? src[e] : make_uint4(0u, 0u, 0u, 0u);
+    const uint8_t* __restrict__ src = T.pop.slot + (long long)b0 * ns;
+    for (int e = threadIdx.x; e < KB * ns; e += kThreads) {
+      const int j = e / KB, bb = e - j * KB;
+      sl[e] = (bb < nb) ? src[(long long)bb * ns + j] : (uint8_t)0;
     }
   }
   __syncthreads();
@@ -137,18 +146,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_plain(const __grid_constan
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const int j = j0 + c;
-        coff[bb][c] = bb * pp + ((j < n) ? (int)sl[bb * ns + j] : 0);
+        coff[bb][c] = bb * pp + ((j < n) ? (int)sl[j * KB + bb] : 0);
       }
     for (int i = r0 + grp; i < r1; i += 32 * G) {
       float part[KB];
 #pragma unroll
       for (int bb = 0; bb < KB; ++bb) part[bb] = 0.f;
       const int iend = min(r1, i + 32 * G);
-      for (int ii = i; ii < iend; ii += G) {
-        const float4 w = __ldg(reinterpret_cast<const float4*>(W + (long long)ii * ldw + j0));
+      // rows ascending; the W loads of four rows are issued before their sums
+      auto row_sum = [&](const float4& w, int ii) {
+        const unsigned long long codes = node_codes<KB>(sl + ii * KB);
 #pragma unroll
         for (int bb = 0; bb < KB; ++bb) {
-          const float* row = tab + (int)sl[bb * ns + ii] * p;
+          const float* row = tab + (int)((codes >> (8 * bb)) & 0xFFu) * p;
           float s = part[bb];
           s = fmaf(w.x, row[coff[bb][0]], s);
           s = fmaf(w.y, row[coff[bb][1]], s);
@@ -156,7 +166,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_plain(const __grid_constan
           s = fmaf(w.w, row[coff[bb][3]], s);
           part[bb] = s;
         }
+      };
+      int ii = i;
+      for (; ii + 3 * G < iend; ii += 4 * G) {
+        float4 w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) w[u] = __ldg(reinterpret_cast<const float4*>(W + (long long)(ii + u * G) * ldw + j0));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) row_sum(w[u], ii + u * G);
       }
+      for (; ii < iend; ii += G) row_sum(__ldg(reinterpret_cast<const float4*>(W + (long long)ii * ldw + j0)), ii);
 #pragma unroll
       for (int bb = 0; bb < KB; ++bb) acc[bb] += part[bb];
     }
