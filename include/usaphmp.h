@@ -240,8 +240,9 @@ int usaphmp_ga_run_profiled(usaphmp_t h, int32_t generations, void* stream, doub
  * `max_active` (<= 64) run and the device bytes of the running ones
  * (usaphmp_server_footprint) stay within `hbm_budget_bytes`; a request that
  * alone exceeds the budget finishes with USAPHMP_EBUSY.  Each
- * usaphmp_server_step admits what fits, then runs one generation (§5) of
- * every running request with one launch per kernel over all of them, then
+ * usaphmp_server_step admits what fits, then runs up to 8 generations (§5)
+ * of every running request -- as many as every one of them still needs, at
+ * most 8 -- with one launch per kernel and generation over all of them, then
  * rescores (fp64) and releases the requests that have run all their
  * generations.  A request's result does not depend on which other requests
  * ran beside it.  The server is not thread-safe.

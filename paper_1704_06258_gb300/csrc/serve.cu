@@ -11,6 +11,7 @@
 // kept for polling and its device memory released.  Each request's
 // arithmetic depends only on its own data, so its result is the same alone
 // and in any mix.
+#include <algorithm>
 #include <chrono>
 #include <deque>
 #include <map>
@@ -51,6 +52,11 @@ struct Finished {
 
 }  // namespace
 
+// Generations a step runs for the running requests at most: fewer host round
+// trips per generation at the cost of admitting new requests only between
+// steps.
+constexpr int kGensPerTick = 8;
+
 struct usaphmp_server_s {
   size_t budget = 0, used = 0;
   int max_active = 0, path = 0, num_sms = 0;
@@ -58,6 +64,7 @@ struct usaphmp_server_s {
   uint32_t* d_status = nullptr;
   Task* d_tasks = nullptr;
   std::vector<Task> h_tasks;
+  bool tasks_dirty = true;  // the device task table no longer matches `active`
   std::deque<Request> pending;
   std::vector<Request> active;
   std::map<int64_t, Finished> done;
@@ -190,47 +197,60 @@ int usaphmp_server_step(usaphmp_server_t s, int32_t* n_active, int32_t* n_pendin
     s->pending.pop_front();
     const int rc = admit(s, r);
     if (rc != USAPHMP_OK) return rc;
-    if (r.h) s->active.push_back(std::move(r));
+    if (r.h) {
+      s->active.push_back(std::move(r));
+      s->tasks_dirty = true;
+    }
   }
   // requests asking for no generation finish at once
   for (size_t i = 0; i < s->active.size();) {
     if (s->active[i].gens >= s->active[i].G) {
       finish(s, s->active[i], USAPHMP_OK, "");
       s->active.erase(s->active.begin() + i);
+      s->tasks_dirty = true;
     } else {
       ++i;
     }
   }
   if (!s->active.empty()) {
-    // one generation of every running request, one launch per kernel
-    s->h_tasks.clear();
+    // up to kGensPerTick generations of every running request (no more than
+    // any of them still needs), one launch per kernel over all of them; the
+    // task table goes to the device only when the running set has changed
     bool tc = false;
-    for (auto& r : s->active) {
-      s->h_tasks.push_back(handle_ga_task(r.h));
-      tc = handle_uses_tc(r.h);
+    if (s->tasks_dirty) {
+      s->h_tasks.clear();
+      for (auto& r : s->active) s->h_tasks.push_back(handle_ga_task(r.h));
+      cudaError_t e = cudaMemcpyAsync(s->d_tasks, s->h_tasks.data(), sizeof(Task) * s->h_tasks.size(),
+                                      cudaMemcpyHostToDevice, s->stream);
+      if (e != cudaSuccess) return report_error(USAPHMP_ECUDA, std::string("task upload: ") + cudaGetErrorString(e));
+      s->tasks_dirty = false;
     }
-    const int count = (int)s->h_tasks.size();
-    cudaError_t e = cudaMemcpyAsync(s->d_tasks, s->h_tasks.data(), sizeof(Task) * count, cudaMemcpyHostToDevice,
-                                    s->stream);
-    if (e != cudaSuccess) return report_error(USAPHMP_ECUDA, std::string("task upload: ") + cudaGetErrorString(e));
-    const TaskSet ts{s->d_tasks, s->h_tasks.data(), count};
-    launch_children(ts, s->stream);
-    launch_alloc(ts, true, tc, s->stream);
-    if (tc)
-      launch_eval_tc(ts, s->num_sms, s->d_status, s->stream);
-    else
-      launch_eval_plain(ts, s->stream);
-    launch_reduce_select(ts, s->stream);
-    e = cudaGetLastError();
+    int k = kGensPerTick;
+    for (auto& r : s->active) {
+      tc = handle_uses_tc(r.h);
+      k = std::min(k, r.G - r.gens);
+    }
+    const TaskSet ts{s->d_tasks, s->h_tasks.data(), (int)s->h_tasks.size()};
+    for (int g = 0; g < k; ++g) {
+      launch_children(ts, s->stream);
+      launch_alloc(ts, true, tc, s->stream);
+      if (tc)
+        launch_eval_tc(ts, s->num_sms, s->d_status, s->stream);
+      else
+        launch_eval_plain(ts, s->stream);
+      launch_reduce_select(ts, s->stream);
+    }
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return report_error(USAPHMP_ECUDA, std::string("generation launch: ") + cudaGetErrorString(e));
     for (auto& r : s->active) {
-      ++r.gens;
-      handle_note_generations(r.h, 1);
+      r.gens += k;
+      handle_note_generations(r.h, k);
     }
     for (size_t i = 0; i < s->active.size();) {
       if (s->active[i].gens >= s->active[i].G) {
         finish(s, s->active[i], USAPHMP_OK, "");
         s->active.erase(s->active.begin() + i);
+        s->tasks_dirty = true;
       } else {
         ++i;
       }
