@@ -44,7 +44,8 @@ enum {
   USAPHMP_ECUDA = -4,         /* a CUDA call failed (message names it) */
   USAPHMP_ETIMEOUT = -5,      /* a device-side wait gave up (kernel returned early) */
   USAPHMP_EBUSY = -6,         /* resource limit reached (admission refused) */
-  USAPHMP_EIO = -7            /* a file could not be written */
+  USAPHMP_EIO = -7,           /* a file could not be written */
+  USAPHMP_ECANCELED = -8      /* the request was cancelled (usaphmp_server_cancel) */
 };
 
 /* Transfer leg of objective (1) between the hubs h(i) and h(j) (eq. 4 lets
@@ -199,6 +200,21 @@ int usaphmp_select_dev(usaphmp_t h, int32_t R, int32_t P, int32_t g, const uint3
 int usaphmp_ga_islands(usaphmp_t h, uint32_t* masks, float* fit, void* stream);
 int usaphmp_ga_merge(usaphmp_t h, const uint32_t* mask, float fit, void* stream);
 
+/* Checkpoint / resume of the GA between generations.  The state is small:
+ * the island ancestors and their fitness, the best-ever solution, the
+ * generation counter and the seed (the random streams are counter-based, so
+ * a resumed run draws exactly what an uninterrupted one draws).  A state
+ * saved by usaphmp_ga_save (after usaphmp_ga_begin) and loaded by
+ * usaphmp_ga_load into a handle of the same instance size and GA parameters
+ * continues the run bit for bit.  bytes = usaphmp_ga_state_bytes for the
+ * handle's current parameters; a buffer of another size, with another
+ * layout version or saved with other n, p, islands, island_size, n1, elitist
+ * or island_offset gives USAPHMP_EINVAL (nothing changed).  Both calls
+ * synchronise `stream`. */
+int usaphmp_ga_state_bytes(usaphmp_t h, int64_t* bytes);
+int usaphmp_ga_save(usaphmp_t h, void* buf, int64_t bytes, void* stream);
+int usaphmp_ga_load(usaphmp_t h, const void* buf, int64_t bytes, void* stream);
+
 /* Allocation local search for fixed hubs, in fp64 (§4.1 allocates every
  * spoke to its nearest hub, which is not always the cheapest allocation for
  * those hubs).  A sweep visits the spokes in ascending node order and moves
@@ -264,6 +280,13 @@ int usaphmp_server_step(usaphmp_server_t s, int32_t* n_active, int32_t* n_pendin
  * < 0: the request failed (message in usaphmp_last_error). */
 int usaphmp_server_poll(usaphmp_server_t s, int64_t ticket, usaphmp_result* out);
 
+/* Cancels a request between steps: a queued one leaves the queue, a running
+ * one stops (its slot and device memory are freed at once).  Its poll then
+ * returns USAPHMP_ECANCELED.  USAPHMP_EINVAL for a ticket that is not queued
+ * or running (unknown, finished or already cancelled).  Synchronises the
+ * server's stream when the request is running. */
+int usaphmp_server_cancel(usaphmp_server_t s, int64_t ticket);
+
 /* Device bytes a request of this shape holds while it runs. */
 int usaphmp_server_footprint(int32_t n, int32_t p, int32_t islands, int32_t island_size, int64_t* bytes);
 
@@ -325,6 +348,22 @@ int usaphmp_tile_cache_lookup(const char* path, const char* device, int32_t n, i
                               usaphmp_tile* out, double* ms);
 int usaphmp_tile_cache_store(const char* path, const char* device, int32_t n, int32_t p, int32_t B,
                              const usaphmp_tile* tile, double ms);
+
+/* ---------------------------------------------------------------------------
+ * Testing hooks (failure detection without a GPU fault).
+ *
+ * usaphmp_debug_fail_allocations: the next `after` device allocations of the
+ * library succeed and the one after fails (the call reports USAPHMP_ENOMEM);
+ * after < 0 turns the injection off.  Process-wide.
+ *
+ * usaphmp_selftest_wait_timeout: runs one small kernel whose threads wait,
+ * with the bounded waits of the tensor-core evaluator and a limit of
+ * limit_ns (1e3 .. 1e10), on a barrier that nothing completes.  Returns
+ * USAPHMP_ETIMEOUT when the waits gave up as they must (status holds the
+ * device status word, elapsed_ns the time the waits took); USAPHMP_ECUDA
+ * otherwise.  The CUDA context stays usable. */
+int usaphmp_debug_fail_allocations(int32_t after);
+int usaphmp_selftest_wait_timeout(int64_t limit_ns, uint32_t* status, int64_t* elapsed_ns);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free entry point.  The paper has no counterpart: this exists for

@@ -26,7 +26,8 @@ SCALE_RAW = 0
 SCALE_MILLI = 1
 SCALE_PER_FLOW = 2
 
-ERRORS = {-1: "EINVAL", -2: "EINVAL_CHROM", -3: "ENOMEM", -4: "ECUDA", -5: "ETIMEOUT", -6: "EBUSY", -7: "EIO"}
+ERRORS = {-1: "EINVAL", -2: "EINVAL_CHROM", -3: "ENOMEM", -4: "ECUDA", -5: "ETIMEOUT", -6: "EBUSY", -7: "EIO",
+          -8: "ECANCELED"}
 
 c_i32, c_i64, c_u64, c_f64, c_f32, c_vp = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
                                            ctypes.c_double, ctypes.c_float, ctypes.c_void_p)
@@ -84,7 +85,13 @@ _SIGS = {
     "usaphmp_server_poll": (c_i32, [c_vp, c_i64, ctypes.POINTER(Result)]),
     "usaphmp_server_footprint": (c_i32, [c_i32, c_i32, c_i32, c_i32, ctypes.POINTER(c_i64)]),
     "usaphmp_server_destroy": (None, [c_vp]),
+    "usaphmp_server_cancel": (c_i32, [c_vp, c_i64]),
+    "usaphmp_debug_fail_allocations": (c_i32, [c_i32]),
+    "usaphmp_selftest_wait_timeout": (c_i32, [c_i64, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(c_i64)]),
     "usaphmp_ga_islands": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
+    "usaphmp_ga_state_bytes": (c_i32, [c_vp, ctypes.POINTER(c_i64)]),
+    "usaphmp_ga_save": (c_i32, [c_vp, c_vp, c_i64, c_vp]),
+    "usaphmp_ga_load": (c_i32, [c_vp, c_vp, c_i64, c_vp]),
     "usaphmp_ga_merge": (c_i32, [c_vp, c_vp, c_f32, c_vp]),
     "usaphmp_local_search_dev": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp]),
     "usaphmp_set_tile": (c_i32, [c_vp, ctypes.POINTER(Tile)]),
@@ -130,6 +137,18 @@ def check(rc):
 
 def _ptr(a):
     return a.ctypes.data_as(c_vp)
+
+
+def debug_fail_allocations(after):
+    """usaphmp_debug_fail_allocations (testing hook)."""
+    check(lib().usaphmp_debug_fail_allocations(after))
+
+
+def selftest_wait_timeout(limit_ns):
+    """usaphmp_selftest_wait_timeout: (return code, status word, elapsed ns)."""
+    st, el = ctypes.c_uint32(), c_i64()
+    rc = lib().usaphmp_selftest_wait_timeout(int(limit_ns), ctypes.byref(st), ctypes.byref(el))
+    return rc, st.value, el.value
 
 
 def rescore_fp64_noalloc(n, p, B, W_ptr, C_ptr, chi, alpha, delta, hubs_ptr, slot_ptr, cost_ptr, stream=0):
@@ -294,6 +313,19 @@ class Instance:
         check(lib().usaphmp_ga_run_profiled(self.h, generations, stream, acc))
         return dict(zip(STAGES, list(acc)))
 
+    def ga_save(self, stream=0):
+        """usaphmp_ga_save: the GA state as bytes."""
+        nb = c_i64()
+        check(lib().usaphmp_ga_state_bytes(self.h, ctypes.byref(nb)))
+        buf = ctypes.create_string_buffer(nb.value)
+        check(lib().usaphmp_ga_save(self.h, buf, nb.value, stream))
+        return buf.raw
+
+    def ga_load(self, state, stream=0):
+        """usaphmp_ga_load: continue from a saved state."""
+        buf = ctypes.create_string_buffer(bytes(state), len(state))
+        check(lib().usaphmp_ga_load(self.h, buf, len(state), stream))
+
     def ga_islands(self, stream=0):
         """usaphmp_ga_islands: (masks uint32 [R, nw], fitness float32 [R])."""
         R = self.params["islands"]
@@ -340,6 +372,10 @@ class Server:
         a, q = c_i32(), c_i32()
         check(lib().usaphmp_server_step(self.h, ctypes.byref(a), ctypes.byref(q)))
         return a.value, q.value
+
+    def cancel(self, ticket):
+        """usaphmp_server_cancel."""
+        check(lib().usaphmp_server_cancel(self.h, ticket))
 
     def poll(self, ticket):
         """None while running; the result dict once finished (raises on failure)."""

@@ -8,6 +8,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstring>
 #include <string>
@@ -45,8 +46,17 @@ int cuda_fail(cudaError_t e, const char* what) {
     if (r_ != USAPHMP_OK) return r_; \
   } while (0)
 
+// Testing hook (usaphmp_debug_fail_allocations): device allocations left
+// before one fails; negative = never.
+std::atomic<int> g_fail_after{-1};
+
 template <class T>
 cudaError_t dalloc(T** p, size_t count) {
+  int left = g_fail_after.load();
+  while (left >= 0) {
+    if (left == 0) return cudaErrorMemoryAllocation;
+    if (g_fail_after.compare_exchange_weak(left, left - 1)) break;
+  }
   return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * std::max<size_t>(count, 1));
 }
 
@@ -393,6 +403,7 @@ int ensure_ga(usaphmp_s* h) {
   RET(ensure_pop(h, h->ga, B));
   RET(ensure_pop(h, h->one, 1));
   if (h->ga_R != R || h->ga_P != P || !h->anc) {
+    h->ga_R = h->ga_P = 0;  // stays 0 unless every buffer below is allocated
     dfree(h->anc); dfree(h->anc_fit); dfree(h->best); dfree(h->best_fit); dfree(h->gen); dfree(h->mask0);
     dfree(h->done);
     CK(dalloc(&h->done, 1));
@@ -897,6 +908,113 @@ int usaphmp_ga_run_profiled(usaphmp_t h, int32_t generations, void* stream, doub
     stage_ms[5] += all;
     h->ga_evals += B;
   }
+  return USAPHMP_OK;
+}
+
+namespace {
+// Host layout of a saved GA state: this header, then anc [R][nw] u32,
+// anc_fit [R] f32, best [nw] u32, best_fit f32, padded to 8 bytes.
+struct GaStateHeader {
+  uint32_t magic;  // "USGA"
+  uint32_t version;
+  int32_t n, p, nw, R, P, n1, elitist, island_offset;
+  uint64_t seed;
+  int32_t gen;
+  int32_t reserved;
+  int64_t evals;
+};
+constexpr uint32_t kGaStateMagic = 0x41475355u;
+constexpr uint32_t kGaStateVersion = 1;
+
+int64_t ga_state_bytes(const usaphmp_s* h) {
+  const int64_t R = h->prm.islands, nw = h->nw;
+  const int64_t b = (int64_t)sizeof(GaStateHeader) + 4 * (R * nw + R + nw + 1);
+  return (b + 7) / 8 * 8;
+}
+}  // namespace
+
+int usaphmp_debug_fail_allocations(int32_t after) {
+  g_fail_after.store(after < 0 ? -1 : after);
+  return USAPHMP_OK;
+}
+
+int usaphmp_selftest_wait_timeout(int64_t limit_ns, uint32_t* status, int64_t* elapsed_ns) {
+  if (!status || !elapsed_ns) return fail(USAPHMP_EINVAL, "NULL argument");
+  if (limit_ns < 1000 || limit_ns > 10000000000ll) return fail(USAPHMP_EINVAL, "limit_ns must be in [1e3, 1e10]");
+  unsigned long long el = 0;
+  const int rc = selftest_wait_timeout((uint64_t)limit_ns, status, &el);
+  if (rc != USAPHMP_OK) return rc;
+  *elapsed_ns = (int64_t)el;
+  if (*status & 0x80000000u) return fail(USAPHMP_ECUDA, "wait self-test: a wait on an incomplete barrier succeeded");
+  if (!(*status & kStatusTimeout)) return fail(USAPHMP_ECUDA, "wait self-test: the waits did not time out");
+  return fail(USAPHMP_ETIMEOUT, "wait self-test: the bounded waits gave up as expected");
+}
+
+int usaphmp_ga_state_bytes(usaphmp_t h, int64_t* bytes) {
+  if (!h || !bytes) return fail(USAPHMP_EINVAL, "NULL argument");
+  *bytes = ga_state_bytes(h);
+  return USAPHMP_OK;
+}
+
+int usaphmp_ga_save(usaphmp_t h, void* buf, int64_t bytes, void* stream) {
+  if (!h || !buf) return fail(USAPHMP_EINVAL, "NULL argument");
+  if (!h->ga_ready) return fail(USAPHMP_EINVAL, "usaphmp_ga_begin first");
+  if (bytes != ga_state_bytes(h)) return fail(USAPHMP_EINVAL, "usaphmp_ga_save: buffer size differs from usaphmp_ga_state_bytes");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Task& t = h->ga_task;
+  GaStateHeader hd{};
+  hd.magic = kGaStateMagic;
+  hd.version = kGaStateVersion;
+  hd.n = h->n; hd.p = h->p; hd.nw = h->nw;
+  hd.R = t.ga.R; hd.P = t.ga.P; hd.n1 = t.ga.N1; hd.elitist = t.ga.elitist; hd.island_offset = t.ga.island_offset;
+  hd.seed = t.ga.seed;
+  hd.evals = h->ga_evals;
+  char* out = static_cast<char*>(buf);
+  std::memset(out, 0, (size_t)bytes);
+  uint32_t* anc = reinterpret_cast<uint32_t*>(out + sizeof(GaStateHeader));
+  float* anc_fit = reinterpret_cast<float*>(anc + (size_t)hd.R * hd.nw);
+  uint32_t* best = reinterpret_cast<uint32_t*>(anc_fit + hd.R);
+  float* best_fit = reinterpret_cast<float*>(best + hd.nw);
+  CK(cudaMemcpyAsync(anc, h->anc, sizeof(uint32_t) * hd.R * hd.nw, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(anc_fit, h->anc_fit, sizeof(float) * hd.R, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(best, h->best, sizeof(uint32_t) * hd.nw, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(best_fit, h->best_fit, sizeof(float), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&hd.gen, h->gen, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::memcpy(out, &hd, sizeof(hd));
+  return USAPHMP_OK;
+}
+
+int usaphmp_ga_load(usaphmp_t h, const void* buf, int64_t bytes, void* stream) {
+  if (!h || !buf) return fail(USAPHMP_EINVAL, "NULL argument");
+  if (bytes != ga_state_bytes(h)) return fail(USAPHMP_EINVAL, "usaphmp_ga_load: buffer size differs from usaphmp_ga_state_bytes");
+  GaStateHeader hd;
+  std::memcpy(&hd, buf, sizeof(hd));
+  if (hd.magic != kGaStateMagic || hd.version != kGaStateVersion)
+    return fail(USAPHMP_EINVAL, "usaphmp_ga_load: not a saved GA state of this layout version");
+  if (hd.n != h->n || hd.p != h->p || hd.nw != h->nw || hd.R != h->prm.islands || hd.P != h->prm.island_size ||
+      hd.n1 != h->prm.n1 || hd.elitist != h->prm.elitist || hd.island_offset != h->prm.island_offset)
+    return fail(USAPHMP_EINVAL, "usaphmp_ga_load: the state was saved with another instance size or GA parameters");
+  if (hd.gen < 0) return fail(USAPHMP_EINVAL, "usaphmp_ga_load: negative generation");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  RET(ensure_ga(h));
+  drop_graph(h);
+  const char* in = static_cast<const char*>(buf);
+  const uint32_t* anc = reinterpret_cast<const uint32_t*>(in + sizeof(GaStateHeader));
+  const float* anc_fit = reinterpret_cast<const float*>(anc + (size_t)hd.R * hd.nw);
+  const uint32_t* best = reinterpret_cast<const uint32_t*>(anc_fit + hd.R);
+  const float* best_fit = reinterpret_cast<const float*>(best + hd.nw);
+  CK(cudaMemcpyAsync(h->anc, anc, sizeof(uint32_t) * hd.R * hd.nw, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->anc_fit, anc_fit, sizeof(float) * hd.R, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->best, best, sizeof(uint32_t) * hd.nw, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->best_fit, best_fit, sizeof(float), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->gen, &hd.gen, sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(h->done, 0, sizeof(int), s));
+  CK(cudaStreamSynchronize(s));
+  RET(reset_status(h, s));
+  h->ga_task = ga_task_of(h, hd.seed);
+  h->ga_evals = hd.evals;
+  h->ga_ready = true;
   return USAPHMP_OK;
 }
 

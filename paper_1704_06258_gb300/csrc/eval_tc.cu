@@ -28,6 +28,8 @@
 // of one tile overlap the MMAs of the next.  Every wait is bounded: after
 // kTimeoutNs the kernel raises kStatusTimeout, drains its own copies and
 // MMAs, frees TMEM and returns.
+#include "usaphmp.h"
+
 #include "common.cuh"
 #include "kernels.cuh"
 #include "tc_ptx.cuh"
@@ -87,14 +89,15 @@ struct Bars {
 
 // Single-thread bounded wait.  Returns false on timeout or when another role
 // has already aborted.
-__device__ __forceinline__ bool wait_one(uint32_t bar, uint32_t parity, volatile int* abort_flag, uint32_t* status) {
+__device__ __forceinline__ bool wait_one(uint32_t bar, uint32_t parity, volatile int* abort_flag, uint32_t* status,
+                                         uint64_t limit_ns = kTimeoutNs) {
   if (ptx::mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = ptx::globaltimer();
   for (uint32_t i = 1;; ++i) {
     if (ptx::mbar_try_wait(bar, parity)) return true;
     if ((i & 255u) == 0) {
       if (*abort_flag) return false;
-      if (ptx::globaltimer() - t0 > kTimeoutNs) {
+      if (ptx::globaltimer() - t0 > limit_ns) {
         *abort_flag = 1;
         atomicOr(status, kStatusTimeout);
         return false;
@@ -111,7 +114,8 @@ __device__ void wait_drain(uint32_t bar, uint32_t parity) {
 }
 
 // Warp-collective bounded wait: every lane returns the same answer.
-__device__ __forceinline__ bool wait_warp(uint32_t bar, uint32_t parity, volatile int* abort_flag, uint32_t* status) {
+__device__ __forceinline__ bool wait_warp(uint32_t bar, uint32_t parity, volatile int* abort_flag, uint32_t* status,
+                                          uint64_t limit_ns = kTimeoutNs) {
   const uint64_t t0 = ptx::globaltimer();
   for (uint32_t i = 0;; ++i) {
     const bool ok = ptx::mbar_try_wait(bar, parity);
@@ -120,7 +124,7 @@ __device__ __forceinline__ bool wait_warp(uint32_t bar, uint32_t parity, volatil
       int stop = 0;
       if ((threadIdx.x & 31) == 0) {
         stop = *abort_flag;
-        if (!stop && ptx::globaltimer() - t0 > kTimeoutNs) {
+        if (!stop && ptx::globaltimer() - t0 > limit_ns) {
           *abort_flag = 1;
           atomicOr(status, kStatusTimeout);
           stop = 1;
@@ -567,6 +571,52 @@ void launch_eval_tc(const TaskSet& ts, int num_sms, uint32_t* status, cudaStream
   if (total == 0) return;
   const int grid = total < num_sms ? total : num_sms;
   k_eval_tc<<<grid, kThreads, kSmemBytes, s>>>(tp, total, status, L);
+}
+
+// Self-test of the bounded waits: the warps of one block wait on an mbarrier
+// that nothing completes, one thread with wait_one and one warp with
+// wait_warp, under a short limit.  Both must give up: the first records
+// kStatusTimeout and raises the abort flag, the second stops on the flag
+// (or on its own limit); bit 31 of *status marks a wait that wrongly
+// succeeded.  The kernel then returns normally.
+__global__ void k_wait_selftest(uint64_t limit_ns, uint32_t* status, unsigned long long* elapsed_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  const uint32_t b = ptx::smem_u32(&bar);
+  if (threadIdx.x == 0) {
+    ptx::mbar_init(b, 1);
+    abort_flag = 0;
+    ptx::fence_mbar_init();
+  }
+  __syncthreads();
+  const uint64_t t0 = ptx::globaltimer();
+  bool ok = false;
+  if (threadIdx.x < 32) {
+    if (threadIdx.x == 0) ok = wait_one(b, 0, &abort_flag, status, limit_ns);
+  } else {
+    ok = wait_warp(b, 0, &abort_flag, status, limit_ns);
+  }
+  if (ok) atomicOr(status, 0x80000000u);
+  __syncthreads();
+  if (threadIdx.x == 0) *elapsed_ns = ptx::globaltimer() - t0;
+}
+
+int selftest_wait_timeout(uint64_t limit_ns, uint32_t* status, unsigned long long* elapsed_ns) {
+  uint32_t* d_status = nullptr;
+  unsigned long long* d_el = nullptr;
+  cudaError_t e = cudaMalloc(&d_status, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&d_el, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(d_status, 0, sizeof(uint32_t));
+  if (e == cudaSuccess) {
+    k_wait_selftest<<<1, 64>>>(limit_ns, d_status, d_el);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(status, d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(elapsed_ns, d_el, sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+  cudaFree(d_status);
+  cudaFree(d_el);
+  return e == cudaSuccess ? 0 : report_error(USAPHMP_ECUDA, std::string("wait self-test: ") + cudaGetErrorString(e));
 }
 
 }  // namespace usaphmp

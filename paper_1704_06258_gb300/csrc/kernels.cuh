@@ -97,6 +97,8 @@ size_t tc_slab_bytes(const TcTile& t);
 void launch_eval_tc(const TaskSet& ts, int num_sms, uint32_t* status, cudaStream_t s,
                     const TcTile& tile = TcTile{});
 int tc_part_rows(int n);
+// Runs k_wait_selftest (see eval_tc.cu); 0 or a USAPHMP_E* code.
+int selftest_wait_timeout(uint64_t limit_ns, uint32_t* status, unsigned long long* elapsed_ns);
 void prepare_eval_tc();
 
 // reduce.cu: fit[b] = t12[b] + alpha * (sum of partials, fixed order).

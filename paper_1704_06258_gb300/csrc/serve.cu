@@ -261,6 +261,27 @@ int usaphmp_server_step(usaphmp_server_t s, int32_t* n_active, int32_t* n_pendin
   return USAPHMP_OK;
 }
 
+int usaphmp_server_cancel(usaphmp_server_t s, int64_t ticket) {
+  if (!s) return report_error(USAPHMP_EINVAL, "NULL server");
+  for (auto it = s->pending.begin(); it != s->pending.end(); ++it)
+    if (it->ticket == ticket) {
+      finish(s, *it, USAPHMP_ECANCELED, "cancelled");
+      s->pending.erase(it);
+      return USAPHMP_OK;
+    }
+  for (size_t i = 0; i < s->active.size(); ++i)
+    if (s->active[i].ticket == ticket) {
+      // its last generations may still run on the server's stream
+      const cudaError_t e = cudaStreamSynchronize(s->stream);
+      if (e != cudaSuccess) return report_error(USAPHMP_ECUDA, std::string("cancel: ") + cudaGetErrorString(e));
+      finish(s, s->active[i], USAPHMP_ECANCELED, "cancelled");
+      s->active.erase(s->active.begin() + i);
+      s->tasks_dirty = true;
+      return USAPHMP_OK;
+    }
+  return report_error(USAPHMP_EINVAL, "cancel: ticket " + std::to_string(ticket) + " is not queued or running");
+}
+
 int usaphmp_server_poll(usaphmp_server_t s, int64_t ticket, usaphmp_result* out) {
   if (!s || !out) return report_error(USAPHMP_EINVAL, "NULL argument");
   auto it = s->done.find(ticket);
