@@ -336,6 +336,7 @@ int create_common(usaphmp_s* h, const float* W, const float* C, bool dev, cudaSt
 
 int create_impl(int32_t n, int32_t p, const float* W, const float* C, double chi, double alpha, double delta,
                 bool dev, void* stream, usaphmp_t* out) {
+  const NvtxRange nvtx_range("usaphmp_create");
   if (!out) return fail(USAPHMP_EINVAL, "out is NULL");
   *out = nullptr;
   if (!W || !C) return fail(USAPHMP_EINVAL, "W or C is NULL");
@@ -570,6 +571,7 @@ int usaphmp_get_tile(usaphmp_t h, usaphmp_tile* tile) {
 
 int usaphmp_autotune(usaphmp_t h, int32_t reps, const char* cache_path, usaphmp_tile* chosen, double* chosen_ms,
                      double* default_ms, int32_t* from_cache) {
+  const NvtxRange nvtx_range("usaphmp_autotune");
   if (!h) return fail(USAPHMP_EINVAL, "NULL handle");
   if (reps < 1 || reps > 1000) return fail(USAPHMP_EINVAL, "reps must be in [1, 1000]");
   if (from_cache) *from_cache = 0;
@@ -656,6 +658,7 @@ int usaphmp_get_params(usaphmp_t h, usaphmp_params* prm) {
 }
 
 int usaphmp_eval_dev(usaphmp_t h, int32_t B, const int32_t* hubs, const int32_t* S, float* fitness, void* stream) {
+  const NvtxRange nvtx_range("usaphmp_eval_dev");
   if (!h) return fail(USAPHMP_EINVAL, "NULL handle");
   if (B < 0) return fail(USAPHMP_EINVAL, "B < 0");
   if (B == 0) return USAPHMP_OK;
@@ -664,6 +667,7 @@ int usaphmp_eval_dev(usaphmp_t h, int32_t B, const int32_t* hubs, const int32_t*
 }
 
 int usaphmp_eval(usaphmp_t h, int32_t B, const int32_t* hubs, const int32_t* S, double* fitness) {
+  const NvtxRange nvtx_range("usaphmp_eval");
   if (!h) return fail(USAPHMP_EINVAL, "NULL handle");
   if (B < 0) return fail(USAPHMP_EINVAL, "B < 0");
   if (B == 0) return USAPHMP_OK;
@@ -788,6 +792,7 @@ int usaphmp_select_dev(usaphmp_t h, int32_t R, int32_t P, int32_t g, const uint3
 
 int usaphmp_local_search_dev(usaphmp_t h, int32_t B, const int32_t* hubs, uint8_t* slot, int32_t max_sweeps,
                              int32_t* moves, int32_t* sweeps, void* stream) {
+  const NvtxRange nvtx_range("usaphmp_local_search_dev");
   if (!h || !hubs || !slot) return fail(USAPHMP_EINVAL, "NULL argument");
   if (B <= 0) return B == 0 ? USAPHMP_OK : fail(USAPHMP_EINVAL, "B < 0");
   if (max_sweeps < 1) return fail(USAPHMP_EINVAL, "max_sweeps must be >= 1");
@@ -805,6 +810,7 @@ int usaphmp_local_search_dev(usaphmp_t h, int32_t B, const int32_t* hubs, uint8_
 
 int usaphmp_rescore_fp64_dev(usaphmp_t h, int32_t B, const int32_t* hubs, const uint8_t* slot, double* cost,
                              void* stream) {
+  const NvtxRange nvtx_range("usaphmp_rescore_fp64_dev");
   if (!h || !hubs || !slot || !cost) return fail(USAPHMP_EINVAL, "NULL argument");
   if (B <= 0) return B == 0 ? USAPHMP_OK : fail(USAPHMP_EINVAL, "B < 0");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -829,6 +835,7 @@ int usaphmp_rescore_fp64_dev(usaphmp_t h, int32_t B, const int32_t* hubs, const 
 }
 
 int usaphmp_ga_begin(usaphmp_t h, uint64_t seed, void* stream) {
+  const NvtxRange nvtx_range("usaphmp_ga_begin");
   if (!h) return fail(USAPHMP_EINVAL, "NULL handle");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   RET(ensure_ga(h));
@@ -848,6 +855,7 @@ int usaphmp_ga_begin(usaphmp_t h, uint64_t seed, void* stream) {
 }
 
 int usaphmp_ga_run(usaphmp_t h, int32_t generations, void* stream) {
+  const NvtxRange nvtx_range("usaphmp_ga_run");
   if (!h) return fail(USAPHMP_EINVAL, "NULL handle");
   if (!h->ga_ready) return fail(USAPHMP_EINVAL, "usaphmp_ga_begin first");
   if (generations < 0) return fail(USAPHMP_EINVAL, "generations < 0");
@@ -874,6 +882,7 @@ int usaphmp_ga_run(usaphmp_t h, int32_t generations, void* stream) {
 }
 
 int usaphmp_ga_run_profiled(usaphmp_t h, int32_t generations, void* stream, double* stage_ms) {
+  const NvtxRange nvtx_range("usaphmp_ga_run_profiled");
   if (!h || !stage_ms) return fail(USAPHMP_EINVAL, "NULL argument");
   if (!h->ga_ready) return fail(USAPHMP_EINVAL, "usaphmp_ga_begin first");
   if (generations < 0) return fail(USAPHMP_EINVAL, "generations < 0");
@@ -1050,6 +1059,7 @@ int usaphmp_ga_merge(usaphmp_t h, const uint32_t* mask, float fit, void* stream)
 }
 
 int usaphmp_ga_result(usaphmp_t h, usaphmp_result* best, void* stream) {
+  const NvtxRange nvtx_range("usaphmp_ga_result");
   if (!h || !best) return fail(USAPHMP_EINVAL, "NULL argument");
   if (!h->ga_ready) return fail(USAPHMP_EINVAL, "usaphmp_ga_begin first");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1095,6 +1105,7 @@ int usaphmp_ga_result(usaphmp_t h, usaphmp_result* best, void* stream) {
 }
 
 int usaphmp_solve(usaphmp_t h, int32_t generations, uint64_t seed, usaphmp_result* best) {
+  const NvtxRange nvtx_range("usaphmp_solve");
   if (!h || !best) return fail(USAPHMP_EINVAL, "NULL argument");
   if (generations < 0) return fail(USAPHMP_EINVAL, "generations < 0");
   const auto t0 = std::chrono::steady_clock::now();

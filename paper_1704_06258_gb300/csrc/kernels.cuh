@@ -1,5 +1,6 @@
 // Host-side launchers of the library's kernels (all stream-ordered, no sync).
 #pragma once
+#include <nvtx3/nvToolsExt.h>
 #include <string>
 
 #include "common.cuh"
@@ -50,6 +51,15 @@ inline TaskParam make_param(const TaskSet& ts) {
   tp.bo.o[0] = 0;
   return tp;
 }
+
+// NVTX range over a scope of host code (names the library's calls in a
+// profiler's timeline; costs a branch when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // setup.cu
 void launch_check_values(const float* W, const float* C, int n, int ldw, uint32_t* status, cudaStream_t s);

@@ -189,6 +189,7 @@ int usaphmp_server_submit(usaphmp_server_t s, int32_t n, int32_t p, const float*
 }
 
 int usaphmp_server_step(usaphmp_server_t s, int32_t* n_active, int32_t* n_pending) {
+  const NvtxRange nvtx_range("usaphmp_server_step");
   if (!s) return report_error(USAPHMP_EINVAL, "NULL server");
   // admission, FIFO, by slots and by device bytes
   while (!s->pending.empty() && (int)s->active.size() < s->max_active &&
