@@ -78,7 +78,10 @@ enum {
 /* Evaluators of the transfer term. */
 enum {
   USAPHMP_PATH_PLAIN_FP32 = 0,  /* fp32 CUDA cores, shared-memory gather of C[h(i)][h(j)] */
-  USAPHMP_PATH_SPLIT_BF16 = 1   /* tcgen05 GEMM W*A with W = bf16 hi + lo, fp32 accumulation */
+  USAPHMP_PATH_SPLIT_BF16 = 1,  /* tcgen05 GEMM W*A with W = bf16 hi + lo, fp32 accumulation */
+  USAPHMP_PATH_FP64_REF = 2     /* reference: the pair form of eq. 1 in fp64 for every chromosome
+                                   (the rescoring kernels), rounded to the fp32 fitness; slow,
+                                   for checks; not offered by the server */
 };
 
 typedef struct usaphmp_s* usaphmp_t;

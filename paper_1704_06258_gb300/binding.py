@@ -20,6 +20,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "usaphmp.h")
 
 PATH_PLAIN_FP32 = 0
 PATH_SPLIT_BF16 = 1
+PATH_FP64_REF = 2
 ROUTE_DIRECT = 0
 ROUTE_HUB_PATHS = 1
 SCALE_RAW = 0

@@ -113,6 +113,10 @@ struct usaphmp_s {
   double* d_dist64 = nullptr;  // p*p fp64 hub-path table of the returned solution (hub-path routing)
   double* d_total = nullptr;   // sum of W, fp64 (device)
   double* d_ls = nullptr;      // local-search scratch of the returned solution
+  double* d_part64 = nullptr;  // fp64 reference path: per-chromosome partial sums,
+  double* d_cost64 = nullptr;  //   costs and hub-path tables, for up to cap64 chromosomes
+  double* d_paths64 = nullptr;
+  int cap64 = 0;
   int32_t* d_ls_count = nullptr;  // its moves and sweeps
   double total_flow = 0.0;     // the same on the host
   // evaluation workspace and host-call staging
@@ -158,6 +162,29 @@ DevInst inst_of(const usaphmp_s* h) {
 }
 
 bool use_tc(const usaphmp_s* h) { return h->prm.path == USAPHMP_PATH_SPLIT_BF16; }
+bool use_fp64(const usaphmp_s* h) { return h->prm.path == USAPHMP_PATH_FP64_REF; }
+
+// Scratch of the fp64 reference path for B chromosomes (allocated outside any
+// stream capture: by the calls that evaluate and by ensure_ga).
+int ensure_fp64(usaphmp_s* h, int B) {
+  if (!use_fp64(h)) return USAPHMP_OK;
+  const bool paths = h->prm.routing != USAPHMP_ROUTE_DIRECT;
+  if (h->cap64 >= B && (!paths || h->d_paths64)) return USAPHMP_OK;
+  dfree(h->d_part64); dfree(h->d_cost64); dfree(h->d_paths64);
+  h->cap64 = 0;
+  CK(dalloc(&h->d_part64, (size_t)B * rescore_parts(h->n)));
+  CK(dalloc(&h->d_cost64, (size_t)B));
+  if (paths) CK(dalloc(&h->d_paths64, (size_t)B * h->p * h->p));
+  h->cap64 = B;
+  return USAPHMP_OK;
+}
+
+// fp64 reference evaluation of a task whose hubs and slots are set (the
+// hub-path tables exist whenever the task routes through hubs).
+void launch_fp64_eval(usaphmp_s* h, const Task& task, cudaStream_t s) {
+  launch_rescore(task.in, task.pop.B, task.pop.hubs, task.pop.slot, h->d_part64, h->d_cost64, s, h->d_paths64, 1.0);
+  launch_fit_from_fp64(h->d_cost64, task.pop.fit, task.pop.B, task.pop.out_scale, s);
+}
 
 int part_rows(const usaphmp_s* h, int B) {
   return use_tc(h) ? tc_part_rows(h->n) : plain_rows(h->n, B);
@@ -238,6 +265,12 @@ int reset_status(usaphmp_s* h, cudaStream_t s) {
 // Transfer term + reduction for a task whose hubs/slots/t12/chub are set.
 int run_transfer(usaphmp_s* h, const Task& task, cudaStream_t s) {
   TaskSet ts{nullptr, &task, 1};
+  if (use_fp64(h)) {
+    RET(ensure_fp64(h, task.pop.B));
+    launch_fp64_eval(h, task, s);
+    CK(cudaGetLastError());
+    return USAPHMP_OK;
+  }
   if (use_tc(h))
     launch_eval_tc(ts, h->num_sms, h->d_status, s, h->tile);
   else
@@ -428,6 +461,7 @@ int ensure_ga(usaphmp_s* h) {
   if (!h->d_dist64) CK(dalloc(&h->d_dist64, (size_t)h->p * h->p));
   if (!h->d_ls) CK(dalloc(&h->d_ls, local_search_scratch_doubles(h->n, h->p)));
   if (!h->d_ls_count) CK(dalloc(&h->d_ls_count, 2));
+  RET(ensure_fp64(h, R * P));
   return USAPHMP_OK;
 }
 
@@ -447,11 +481,16 @@ int enqueue_generation(usaphmp_s* h, cudaStream_t s) {
   TaskSet ts{nullptr, &h->ga_task, 1};
   launch_children(ts, s);
   launch_alloc(ts, true, use_tc(h), s);
-  if (use_tc(h))
-    launch_eval_tc(ts, h->num_sms, h->d_status, s, h->tile);
-  else
-    launch_eval_plain(ts, s);
-  launch_reduce_select(ts, s);
+  if (use_fp64(h)) {
+    launch_fp64_eval(h, h->ga_task, s);   // scratch sized by ensure_ga
+    launch_select(ts, s);
+  } else {
+    if (use_tc(h))
+      launch_eval_tc(ts, h->num_sms, h->d_status, s, h->tile);
+    else
+      launch_eval_plain(ts, s);
+    launch_reduce_select(ts, s);
+  }
   CK(cudaGetLastError());
   return USAPHMP_OK;
 }
@@ -510,6 +549,7 @@ void usaphmp_destroy(usaphmp_t h) {
   if (h->tmaps) cudaFree(h->tmaps);
   dfree(h->d_status); dfree(h->d_bad); dfree(h->d_dscratch); dfree(h->d_cost); dfree(h->d_rpart);
   dfree(h->d_dist64); dfree(h->d_total); dfree(h->d_ls); dfree(h->d_ls_count);
+  dfree(h->d_part64); dfree(h->d_cost64); dfree(h->d_paths64);
   if (h->h_status) cudaFreeHost(h->h_status);
   if (h->h_bad) cudaFreeHost(h->h_bad);
   h->ev.release(); h->ga.release(); h->one.release();
@@ -532,7 +572,8 @@ int usaphmp_set_params(usaphmp_t h, const usaphmp_params* prm) {
   if (prm->island_offset < 0 ||
       ((long long)prm->island_offset + prm->islands) * prm->island_size > 0x7fffffffll)
     return fail(USAPHMP_EINVAL, "island_offset must be >= 0 and (island_offset + islands) * island_size < 2^31");
-  if (prm->path != USAPHMP_PATH_PLAIN_FP32 && prm->path != USAPHMP_PATH_SPLIT_BF16)
+  if (prm->path != USAPHMP_PATH_PLAIN_FP32 && prm->path != USAPHMP_PATH_SPLIT_BF16 &&
+      prm->path != USAPHMP_PATH_FP64_REF)
     return fail(USAPHMP_EINVAL, "unknown path");
   if (prm->routing != USAPHMP_ROUTE_DIRECT && prm->routing != USAPHMP_ROUTE_HUB_PATHS)
     return fail(USAPHMP_EINVAL, "unknown routing");
@@ -897,12 +938,17 @@ int usaphmp_ga_run_profiled(usaphmp_t h, int32_t generations, void* stream, doub
     CK(cudaEventRecord(h->prof_ev[1], s));
     launch_alloc(ts, true, use_tc(h), s);
     CK(cudaEventRecord(h->prof_ev[2], s));
-    if (use_tc(h))
+    if (use_fp64(h))
+      launch_fp64_eval(h, h->ga_task, s);
+    else if (use_tc(h))
       launch_eval_tc(ts, h->num_sms, h->d_status, s, h->tile);
     else
       launch_eval_plain(ts, s);
     CK(cudaEventRecord(h->prof_ev[3], s));
-    launch_reduce_select(ts, s);
+    if (use_fp64(h))
+      launch_select(ts, s);
+    else
+      launch_reduce_select(ts, s);
     CK(cudaEventRecord(h->prof_ev[4], s));
     CK(cudaEventRecord(h->prof_ev[5], s));
     CK(cudaGetLastError());

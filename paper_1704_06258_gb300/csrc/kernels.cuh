@@ -131,6 +131,8 @@ void launch_ga_init(const Task& task, const uint32_t* mask0, const float* fit0, 
 void launch_rescore(const DevInst& in, int B, const int32_t* hubs, const uint8_t* slot,
                     double* part, double* cost, cudaStream_t s, double* dist = nullptr, double scale = 1.0);
 int rescore_parts(int n);
+// fit[b] = (float)cost[b] * scale (the fitness of the fp64 reference path).
+void launch_fit_from_fp64(const double* cost, float* fit, int B, float scale, cudaStream_t s);
 
 // local_search.cu: fp64 single-reallocation sweeps for fixed hubs (slots in
 // place); scratch holds local_search_scratch_doubles(n, p) per chromosome.

@@ -92,6 +92,15 @@ __global__ void k_rescore_final(const double* __restrict__ part, int nparts, int
 
 int rescore_parts(int n) { return n < kParts ? n : kParts; }
 
+__global__ void k_fit_from_fp64(const double* __restrict__ cost, float* __restrict__ fit, int B, float scale) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < B) fit[b] = (float)cost[b] * scale;
+}
+
+void launch_fit_from_fp64(const double* cost, float* fit, int B, float scale, cudaStream_t s) {
+  if (B > 0) k_fit_from_fp64<<<(B + 255) / 256, 256, 0, s>>>(cost, fit, B, scale);
+}
+
 void launch_rescore(const DevInst& in, int B, const int32_t* hubs, const uint8_t* slot,
                     double* part, double* cost, cudaStream_t s, double* dist, double scale) {
   if (B <= 0) return;
