@@ -49,3 +49,21 @@ def test_fp64_path_solve_reaches_the_brute_force_nearest_optimum():
         r = gi.solve(100, 2024)
     assert r["cost_fp64"] == pytest.approx(bf["nearest"][0], rel=1e-12)
     assert r["cost_fp32"] == np.float32(r["cost_fp64"])
+
+
+@pytest.mark.parametrize("path", [0, 1], ids=["plain", "split"])
+@pytest.mark.parametrize("seed", [3, 6])
+def test_fast_paths_ga_follows_the_oracle_ga_when_decisions_have_margin(path, seed):
+    """On these runs every selection, merge and best-ever comparison of the
+    oracle GA is decided by a relative margin of at least 4.7e-4 (checked on
+    the oracle side), far above the fp32 / split-bf16 fitness error, so the
+    fast paths must make the same decisions."""
+    inst = synth.urand200(seed=103 + seed, n=36, p=4)
+    R, P, N1, G = 2, 16, 4, 14
+    hubs_o, h_o, cost_o, _ = ga.solve(inst, generations=G, seed=seed, R=R, P=P, N1=N1)
+    with Instance.from_instance(inst) as gi:
+        gi.set_params(islands=R, island_size=P, n1=N1, path=path)
+        r = gi.solve(G, seed)
+    np.testing.assert_array_equal(np.sort(r["hubs"]), np.sort(hubs_o))
+    np.testing.assert_array_equal(r["S"], h_o)
+    assert r["cost_fp64"] == pytest.approx(cost_o, rel=1e-12)
