@@ -38,7 +38,7 @@ L2_FLUSH_BYTES = 512 << 20
 # (None whenever the kernel has changed since that capture).
 K_EVAL_TC_DRAM_BYTES = 14804992
 # the same for one k_alloc launch (profiles/k_alloc_clustered_n1000_p20.md)
-K_ALLOC_DRAM_BYTES = None
+K_ALLOC_DRAM_BYTES = 4378112
 # sm__pipe_tensor_cycles_active (fraction of peak, elapsed) of that k_eval_tc capture
 K_EVAL_TC_TENSOR_ACTIVE = 0.687
 REF_MEMBERS = 16
