@@ -175,11 +175,13 @@ int usaphmp_initial_dev(usaphmp_t h, uint32_t* mask, int32_t* hubs, void* stream
 int usaphmp_children_dev(usaphmp_t h, int32_t R, int32_t P, const uint32_t* anc, uint64_t seed,
                          int32_t g, uint32_t* mask, int32_t* hubs, void* stream);
 
-/* Nearest-hub allocation (§4.1, §5): slot [B][ns] out from ascending hubs. */
+/* Nearest-hub allocation (§4.1, §5): slot [B][ns] out from ascending hubs
+ * (slot 4-byte aligned, else USAPHMP_EINVAL). */
 int usaphmp_allocate_dev(usaphmp_t h, int32_t B, const int32_t* hubs, uint8_t* slot, void* stream);
 
 /* Fitness (fp32 [B] out) of chromosomes in canonical form (ascending hubs,
- * slot codes) by the configured path.  Uses the handle's scratch buffers. */
+ * slot codes [B][ns], 4-byte aligned, padding 0xFF) by the configured path.
+ * Uses the handle's scratch buffers. */
 int usaphmp_eval_slots_dev(usaphmp_t h, int32_t B, const int32_t* hubs, const uint8_t* slot,
                            float* fitness, void* stream);
 

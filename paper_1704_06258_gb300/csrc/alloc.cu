@@ -110,15 +110,40 @@ __global__ void __launch_bounds__(kAllocThreads) k_alloc(const __grid_constant__
     }
     for (int i = (n4 << 2) + threadIdx.x; i < ns; i += blockDim.x) slot[i] = kSlotPad;
   } else {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      int bl = slot_in[i];
-      if (bl >= p) { bad = true; bl = 0; }
-      slot[i] = (uint8_t)bl;
-      const float cih = CT[(long long)hs[bl] * ldw + i];             // C[i, h(i)]
-      const float chi_i = sym ? cih : C[(long long)hs[bl] * ldw + i];  // C[h(i), i]
-      acc += access_term(chi, O[i], cih, delta, D[i], chi_i);
+    // given slots: the same four-node groups and summation order as above,
+    // the four gathers of a group issued before their terms are added
+    const int n4 = (n + 3) >> 2;
+    for (int g = threadIdx.x; g < n4; g += blockDim.x) {
+      const int i0 = g << 2;
+      const uint32_t codes = *reinterpret_cast<const uint32_t*>(slot_in + i0);
+      int bl[4];
+      float cih[4], chi_i[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        bl[k] = (int)((codes >> (8 * k)) & 0xFFu);
+        if (i0 + k < n && bl[k] >= p) bad = true;
+        if (i0 + k >= n || bl[k] >= p) bl[k] = 0;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int i = min(i0 + k, n - 1);
+        cih[k] = CT[(long long)hs[bl[k]] * ldw + i];                       // C[i, h(i)]
+        chi_i[k] = sym ? cih[k] : C[(long long)hs[bl[k]] * ldw + i];      // C[h(i), i]
+      }
+      uint32_t packed = 0u;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int i = i0 + k;
+        if (i < n) {
+          acc += access_term(chi, O[i], cih[k], delta, D[i], chi_i[k]);
+          packed |= (uint32_t)bl[k] << (8 * k);
+        } else {
+          packed |= (uint32_t)kSlotPad << (8 * k);
+        }
+      }
+      *reinterpret_cast<uint32_t*>(slot + i0) = packed;
     }
-    for (int i = n + threadIdx.x; i < ns; i += blockDim.x) slot[i] = kSlotPad;
+    for (int i = (n4 << 2) + threadIdx.x; i < ns; i += blockDim.x) slot[i] = kSlotPad;
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(T.pop.status, kStatusBadChromosome);
   const float s = block_sum(acc, red);

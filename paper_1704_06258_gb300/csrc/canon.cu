@@ -37,18 +37,29 @@ __global__ void k_canon(const int32_t* __restrict__ hubs_in, const int32_t* __re
     if (threadIdx.x == 0) { atomicOr(status, kStatusBadChromosome); atomicMin(bad_index, index_base + b); }
     return;
   }
-  for (int i = threadIdx.x; i < ns; i += blockDim.x) {
-    uint8_t code = kSlotPad;
-    if (i < n) {
-      const int s = S[(long long)b * n + i];
-      if (s < 0 || s >= n || rank[s] == kSlotPad || (rank[i] != kSlotPad && s != i)) {
-        bad = true;
-        code = 0;
-      } else {
-        code = rank[s];
+  // four nodes per thread: their S entries loaded together, one 32-bit store
+  const int32_t* Sb = S + (long long)b * n;
+  for (int g = threadIdx.x; g < (ns >> 2); g += blockDim.x) {
+    const int i0 = g << 2;
+    int sv[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) sv[k] = (i0 + k < n) ? Sb[i0 + k] : 0;
+    uint32_t packed = 0u;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int i = i0 + k, s = sv[k];
+      uint32_t code = kSlotPad;
+      if (i < n) {
+        if (s < 0 || s >= n || rank[s] == kSlotPad || (rank[i] != kSlotPad && s != i)) {
+          bad = true;
+          code = 0;
+        } else {
+          code = rank[s];
+        }
       }
+      packed |= code << (8 * k);
     }
-    slot[(long long)b * ns + i] = code;
+    *reinterpret_cast<uint32_t*>(slot + (long long)b * ns + i0) = packed;
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) {
     atomicOr(status, kStatusBadChromosome);

@@ -781,6 +781,7 @@ int usaphmp_children_dev(usaphmp_t h, int32_t R, int32_t P, const uint32_t* anc,
 
 int usaphmp_allocate_dev(usaphmp_t h, int32_t B, const int32_t* hubs, uint8_t* slot, void* stream) {
   if (!h || !hubs || !slot) return fail(USAPHMP_EINVAL, "NULL argument");
+  if (reinterpret_cast<uintptr_t>(slot) & 3u) return fail(USAPHMP_EINVAL, "slot must be 4-byte aligned");
   if (B <= 0) return B == 0 ? USAPHMP_OK : fail(USAPHMP_EINVAL, "B < 0");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   RET(ensure_pop(h, h->ev, B));
@@ -797,6 +798,7 @@ int usaphmp_allocate_dev(usaphmp_t h, int32_t B, const int32_t* hubs, uint8_t* s
 int usaphmp_eval_slots_dev(usaphmp_t h, int32_t B, const int32_t* hubs, const uint8_t* slot, float* fitness,
                            void* stream) {
   if (!h || !hubs || !slot || !fitness) return fail(USAPHMP_EINVAL, "NULL argument");
+  if (reinterpret_cast<uintptr_t>(slot) & 3u) return fail(USAPHMP_EINVAL, "slot must be 4-byte aligned");
   if (B <= 0) return B == 0 ? USAPHMP_OK : fail(USAPHMP_EINVAL, "B < 0");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   RET(ensure_pop(h, h->ev, B));

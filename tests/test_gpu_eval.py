@@ -203,3 +203,16 @@ def test_host_eval_reports_a_bad_chromosome_in_a_later_chunk():
         S[bad] = S[bad - 1]
         out = gi.eval(hubs, S)
         assert out[bad] == out[bad - 1]
+
+
+def test_misaligned_slot_buffers_are_refused():
+    inst = synth.urand200(seed=35, n=40, p=4)
+    with Instance.from_instance(inst) as gi:
+        hubs = torch.zeros((2, inst.p), dtype=torch.int32, device="cuda")
+        raw = torch.zeros(2 * gi.ns + 4, dtype=torch.uint8, device="cuda")
+        fit = torch.zeros(2, dtype=torch.float32, device="cuda")
+        for call in (lambda: gi.allocate_dev(2, hubs.data_ptr(), raw.data_ptr() + 1, stream()),
+                     lambda: gi.eval_slots_dev(2, hubs.data_ptr(), raw.data_ptr() + 1, fit.data_ptr(), stream())):
+            with pytest.raises(UsaphmpError) as e:
+                call()
+            assert e.value.name == "EINVAL" and "aligned" in str(e.value)
