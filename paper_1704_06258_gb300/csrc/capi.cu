@@ -113,6 +113,8 @@ struct usaphmp_s {
   double* d_dist64 = nullptr;  // p*p fp64 hub-path table of the returned solution (hub-path routing)
   double* d_total = nullptr;   // sum of W, fp64 (device)
   double* d_ls = nullptr;      // local-search scratch of the returned solution
+  float* d_WT = nullptr;       // local search: W transposed and fp64 flow sums [O; D]
+  double* d_OD64 = nullptr;    //   (made on first use)
   double* d_part64 = nullptr;  // fp64 reference path: per-chromosome partial sums,
   double* d_cost64 = nullptr;  //   costs and hub-path tables, for up to cap64 chromosomes
   double* d_paths64 = nullptr;
@@ -176,6 +178,27 @@ int ensure_fp64(usaphmp_s* h, int B) {
   CK(dalloc(&h->d_cost64, (size_t)B));
   if (paths) CK(dalloc(&h->d_paths64, (size_t)B * h->p * h->p));
   h->cap64 = B;
+  return USAPHMP_OK;
+}
+
+// Per-instance inputs of the allocation local search (W transposed, fp64
+// flow sums), made on first use.
+int ensure_ls(usaphmp_s* h, cudaStream_t s) {
+  if (h->d_WT && h->d_OD64) return USAPHMP_OK;
+  dfree(h->d_WT); dfree(h->d_OD64);
+  float* wt = nullptr;
+  double* od = nullptr;
+  CK(dalloc(&wt, (size_t)h->n * h->ldw));
+  const cudaError_t e = dalloc(&od, (size_t)2 * h->n);
+  if (e != cudaSuccess) {
+    dfree(wt);
+    return cuda_fail(e, "dalloc(&od, 2 * n)");
+  }
+  CK(cudaMemsetAsync(wt, 0, sizeof(float) * (size_t)h->n * h->ldw, s));
+  launch_ls_prepare(h->W, h->n, h->ldw, wt, od, s);
+  CK(cudaGetLastError());
+  h->d_WT = wt;
+  h->d_OD64 = od;
   return USAPHMP_OK;
 }
 
@@ -548,7 +571,7 @@ void usaphmp_destroy(usaphmp_t h) {
   dfree(h->W); dfree(h->C); dfree(h->CTbuf); dfree(h->O); dfree(h->D); dfree(h->Whi); dfree(h->Wlo);
   if (h->tmaps) cudaFree(h->tmaps);
   dfree(h->d_status); dfree(h->d_bad); dfree(h->d_dscratch); dfree(h->d_cost); dfree(h->d_rpart);
-  dfree(h->d_dist64); dfree(h->d_total); dfree(h->d_ls); dfree(h->d_ls_count);
+  dfree(h->d_dist64); dfree(h->d_total); dfree(h->d_ls); dfree(h->d_ls_count); dfree(h->d_WT); dfree(h->d_OD64);
   dfree(h->d_part64); dfree(h->d_cost64); dfree(h->d_paths64);
   if (h->h_status) cudaFreeHost(h->h_status);
   if (h->h_bad) cudaFreeHost(h->h_bad);
@@ -840,9 +863,10 @@ int usaphmp_local_search_dev(usaphmp_t h, int32_t B, const int32_t* hubs, uint8_
   if (B <= 0) return B == 0 ? USAPHMP_OK : fail(USAPHMP_EINVAL, "B < 0");
   if (max_sweeps < 1) return fail(USAPHMP_EINVAL, "max_sweeps must be >= 1");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  RET(ensure_ls(h, s));
   double* scratch = nullptr;
   CK(dalloc(&scratch, (size_t)B * local_search_scratch_doubles(h->n, h->p)));
-  launch_local_search(inst_of(h), B, hubs, slot, max_sweeps, scratch, moves, sweeps, s);
+  launch_local_search(inst_of(h), h->d_WT, h->d_OD64, B, hubs, slot, max_sweeps, scratch, moves, sweeps, s);
   cudaError_t e = cudaGetLastError();
   cudaError_t e2 = cudaStreamSynchronize(s);
   cudaFree(scratch);
@@ -1127,8 +1151,9 @@ int usaphmp_ga_result(usaphmp_t h, usaphmp_result* best, void* stream) {
   if (h->prm.local_search > 0) {
     // improve the nearest allocation of the best hubs, then take the fast
     // path's fitness of the improved solution
-    launch_local_search(inst_of(h), 1, h->one.hubs, h->one.slot, h->prm.local_search, h->d_ls, h->d_ls_count,
-                        h->d_ls_count + 1, s);
+    RET(ensure_ls(h, s));
+    launch_local_search(inst_of(h), h->d_WT, h->d_OD64, 1, h->one.hubs, h->one.slot, h->prm.local_search, h->d_ls,
+                        h->d_ls_count, h->d_ls_count + 1, s);
     CK(cudaGetLastError());
     PopBuf pb = popbuf(h, h->one, 1);
     pb.slot_in = h->one.slot;

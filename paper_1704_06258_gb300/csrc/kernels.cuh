@@ -136,9 +136,13 @@ void launch_fit_from_fp64(const double* cost, float* fit, int B, float scale, cu
 
 // local_search.cu: fp64 single-reallocation sweeps for fixed hubs (slots in
 // place); scratch holds local_search_scratch_doubles(n, p) per chromosome.
+// WT = W transposed and OD = [O_i; D_i] in fp64 (2n doubles), made once per
+// instance by launch_ls_prepare.
 size_t local_search_scratch_doubles(int n, int p);
-void launch_local_search(const DevInst& in, int B, const int32_t* hubs, uint8_t* slot, int max_sweeps,
-                         double* scratch, int32_t* moves, int32_t* sweeps, cudaStream_t s);
+void launch_ls_prepare(const float* W, int n, int ldw, float* WT, double* OD, cudaStream_t s);
+void launch_local_search(const DevInst& in, const float* WT, const double* OD, int B, const int32_t* hubs,
+                         uint8_t* slot, int max_sweeps, double* scratch, int32_t* moves, int32_t* sweeps,
+                         cudaStream_t s);
 
 // capi.cu: records the calling thread's last error message; returns `code`.
 int report_error(int code, const std::string& msg);

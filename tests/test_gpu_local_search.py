@@ -42,7 +42,9 @@ def run_gpu(gi, hubs, S, max_sweeps):
 
 
 @pytest.mark.parametrize("seed,n,p,routing", [(5, 40, 3, "direct"), (9, 61, 5, "direct"), (25, 80, 12, "direct"),
-                                              (41, 50, 4, "hubs"), (43, 70, 9, "hubs"), (45, 33, 1, "direct")])
+                                              (41, 50, 4, "hubs"), (43, 70, 9, "hubs"), (45, 33, 1, "direct"),
+                                              # several candidate warps; hub table in global memory at p = 150
+                                              (61, 100, 70, "direct"), (65, 90, 40, "hubs"), (63, 170, 150, "direct")])
 def test_search_matches_oracle(seed, n, p, routing):
     inst = heavy_tailed(seed, n, p, spread=0.8 if routing == "hubs" else 0.0)
     rng = np.random.default_rng(seed)
@@ -118,3 +120,25 @@ def test_bad_arguments():
             gi.set_params(local_search=-1)
         with pytest.raises(UsaphmpError):
             gi.local_search_dev(1, 0, 0, 1)
+
+
+def test_search_matches_oracle_without_fp32_screen():
+    """p = 220: the fp32 hub table no longer fits in shared memory, so every
+    spoke is decided by the fp64 evaluation alone."""
+    seed, n, p = 67, 236, 220
+    inst = heavy_tailed(seed, n, p)
+    rng = np.random.default_rng(seed)
+    hubs = np.stack([np.sort(rng.choice(n, p, replace=False)) for _ in range(2)])
+    starts = []
+    for b in range(2):
+        s = cost.nearest_allocation(inst.C, hubs[b]) if b == 0 else hubs[b][rng.integers(0, p, size=n)]
+        s = s.copy()
+        s[hubs[b]] = hubs[b]
+        starts.append(s)
+    starts = np.stack(starts)
+    with Instance.from_instance(inst) as gi:
+        got, moves, sweeps, _, _ = run_gpu(gi, hubs, starts, 3)
+    for b in range(2):
+        ref, rs, rm = local_search(inst.W, inst.C, inst.chi, inst.alpha, inst.delta, hubs[b], starts[b], 3)
+        np.testing.assert_array_equal(got[b], ref, err_msg=f"chromosome {b}")
+        assert (moves[b], sweeps[b]) == (rm, rs)
