@@ -36,11 +36,11 @@ L2_FLUSH_BYTES = 512 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_eval_tc launch on this
 # workload, from the ncu capture summarised in profiles/k_eval_tc_clustered_n1000_p20.md
 # (None whenever the kernel has changed since that capture).
-K_EVAL_TC_DRAM_BYTES = 14804992
+K_EVAL_TC_DRAM_BYTES = None
 # the same for one k_alloc launch (profiles/k_alloc_clustered_n1000_p20.md)
 K_ALLOC_DRAM_BYTES = 4378112
 # sm__pipe_tensor_cycles_active (fraction of peak, elapsed) of that k_eval_tc capture
-K_EVAL_TC_TENSOR_ACTIVE = 0.687
+K_EVAL_TC_TENSOR_ACTIVE = None
 REF_MEMBERS = 16
 
 
@@ -354,7 +354,7 @@ def large_n_leg(steps, warmup, flush, stream):
                 if name == "split_bf16":
                     row[name]["solve_100_generations_s"] = gi.solve(100, 7)["ms"] * 1e-3
                 if name == "split_bf16":
-                    fl = 4.0 * inst.n * inst.n * p * 2048
+                    fl = tc_flops(inst.n, p, 2048, gi.info()["tc_folded"])
                     row[name]["tensor_tflops"] = fl / (st["transfer"] * 1e-3) / 1e12
                     row[name]["alloc_ms"] = st["allocation"]
                     row[name]["alloc_gbs"] = alloc_bytes(inst.n, p, 2048) / (st["allocation"] * 1e-3) / 1e9
@@ -385,6 +385,15 @@ def routing_leg(steps, warmup, flush, stream):
             if routing == ROUTE_HUB_PATHS:
                 out["rel_err_vs_fp64"] = rel_error_sample(gi, inst, count=32)
     return out
+
+
+def tc_flops(n, p, B, folded):
+    """Algorithmic tensor-core work of one transfer launch: two GEMMs (bf16 hi
+    and lo) of 2 flops per (row, node, slot) over the W entries the kernel
+    multiplies: all n^2, or for a folded operand (symmetric C) the n(n+1)/2 on
+    and above the diagonal."""
+    entries = n * (n + 1) / 2 if folded else n * n
+    return 4.0 * entries * p * B
 
 
 def local_search_leg(stream):
@@ -485,6 +494,7 @@ def run_ours(args):
             plain, _, _ = timed_generations(gi, max(3, min(psteps, 200)), args.warmup, flush, stream, world)
             plain["graph_generation"] = pmean
         gi.set_params(islands=ISLANDS, island_size=ISLAND, n1=10, path=PATH_SPLIT_BF16)
+        folded = bool(gi.info()["tc_folded"])
         if args.tile:                    # a fixed tile shape (profiling runs)
             nt, st, ra = (int(v) for v in args.tile.split(","))
             gi.set_tile(nt, st, ra)
@@ -511,7 +521,7 @@ def run_ours(args):
     value = weak_scaling_value(B, gmean * 1e-3, world)
     plain_ms = max_over_ranks(plain["graph_generation"], world)
     peaks = load_peaks()
-    flops_per_launch = 4.0 * N * N * P_HUBS * B      # 2 GEMMs (hi, lo) x 2 n^2 p per evaluation
+    flops_per_launch = tc_flops(N, P_HUBS, B, folded)
     k1_ms = split["transfer"]
     achieved = flops_per_launch / (k1_ms * 1e-3) / 1e12
     if peaks and peaks.get("bf16_tflops_sustained"):
@@ -529,7 +539,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "path": "split-bf16 tcgen05 (W = bf16 hi + lo, fp32 accumulate)",
+        "config": {"workload": WORKLOAD, "path": "split-bf16 tcgen05 (bf16 hi + lo, fp32 accumulate; " +
+                           ("folded U = W + W^T on and above the diagonal: C is symmetric)" if folded else "W)"),
                    "instance": "8 Gaussian clusters sigma 50 in [0,1e4]^2, W lognormal(0,1.5), W_ii=0, "
                                "C Euclidean, chi=3 alpha=0.75 delta=2, seed 1003+rank",
                    "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MB write, outside the step events)",

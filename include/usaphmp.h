@@ -123,8 +123,10 @@ typedef struct {
 } usaphmp_result;
 
 /* Creates an instance: copies W and C (host, n*n floats each) to the device,
- * checks them (finite, >= 0), computes O, D, the bf16 split of W and whether
- * C is symmetric.  2 <= n <= 16384, 1 <= p <= min(n, 255).  Defines: §3. */
+ * checks them (finite, >= 0), computes O, D, whether C is symmetric and the
+ * bf16 split of the tensor-core operand: W, or for symmetric C the folded
+ * U = W + W^T above the diagonal (W_ii on it), which halves the transfer
+ * GEMM.  2 <= n <= 16384, 1 <= p <= min(n, 255).  Defines: §3. */
 int usaphmp_create(int32_t n, int32_t p, const float* W, const float* C, double chi,
                    double alpha, double delta, usaphmp_t* out);
 
@@ -135,6 +137,17 @@ int usaphmp_create_dev(int32_t n, int32_t p, const float* W, const float* C, dou
 
 int usaphmp_set_params(usaphmp_t h, const usaphmp_params* prm);
 int usaphmp_get_params(usaphmp_t h, usaphmp_params* prm);
+
+/* What the instance holds (read-only). */
+typedef struct {
+  int32_t n, p;
+  int32_t ldw;           /* row stride of the device matrices (n rounded up to 8) */
+  int32_t ns;            /* row stride of the slot codes (n rounded up to 64) */
+  int32_t c_symmetric;   /* 1 when C equals its transpose bit for bit */
+  int32_t tc_folded;     /* 1 when the tensor-core operand is the folded U (only the
+                            K blocks right of each row block's diagonal are multiplied) */
+} usaphmp_info;
+int usaphmp_get_info(usaphmp_t h, usaphmp_info* info);
 
 /* Fitness (objective 1, raw, unscaled) of B chromosomes given on the host:
  * hubs [B][p] node ids (any order), S [B][n] node ids; fitness [B] out.

@@ -49,6 +49,11 @@ class Tile(ctypes.Structure):
     _fields_ = [("ntile", c_i32), ("stages", c_i32), ("raster", c_i32)]
 
 
+class Info(ctypes.Structure):
+    _fields_ = [("n", c_i32), ("p", c_i32), ("ldw", c_i32), ("ns", c_i32), ("c_symmetric", c_i32),
+                ("tc_folded", c_i32)]
+
+
 class UsaphmpError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{ERRORS.get(code, code)}: {msg}")
@@ -97,6 +102,7 @@ _SIGS = {
     "usaphmp_local_search_dev": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp]),
     "usaphmp_set_tile": (c_i32, [c_vp, ctypes.POINTER(Tile)]),
     "usaphmp_get_tile": (c_i32, [c_vp, ctypes.POINTER(Tile)]),
+    "usaphmp_get_info": (c_i32, [c_vp, ctypes.POINTER(Info)]),
     "usaphmp_autotune": (c_i32, [c_vp, c_i32, ctypes.c_char_p, ctypes.POINTER(Tile), ctypes.POINTER(c_f64),
                                  ctypes.POINTER(c_f64), ctypes.POINTER(c_i32)]),
     "usaphmp_tile_cache_lookup": (c_i32, [ctypes.c_char_p, ctypes.c_char_p, c_i32, c_i32, c_i32,
@@ -238,6 +244,12 @@ class Instance:
         """usaphmp_set_tile: tile shape of the tensor-core evaluator."""
         t = Tile(ntile, stages, raster)
         check(lib().usaphmp_set_tile(self.h, ctypes.byref(t)))
+
+    def info(self):
+        """usaphmp_get_info as a dict."""
+        t = Info()
+        check(lib().usaphmp_get_info(self.h, ctypes.byref(t)))
+        return {name: int(getattr(t, name)) for name, _ in Info._fields_}
 
     def get_tile(self):
         t = Tile()

@@ -160,6 +160,7 @@ DevInst inst_of(const usaphmp_s* h) {
   in.chi_d = h->chi; in.alpha_d = h->alpha; in.delta_d = h->delta;
   in.W = h->W; in.C = h->C; in.CT = h->symmetric ? h->C : h->CTbuf;
   in.O = h->O; in.D = h->D; in.Whi = h->Whi; in.Wlo = h->Wlo;
+  in.wtri = h->symmetric;
   return in;
 }
 
@@ -366,7 +367,6 @@ int create_common(usaphmp_s* h, const float* W, const float* C, bool dev, cudaSt
   CK(cudaMemcpy2DAsync(h->C, h->ldw * sizeof(float), C, n * sizeof(float), n * sizeof(float), n, kind, s));
   RET(reset_status(h, s));
   launch_check_values(h->W, h->C, n, h->ldw, h->d_status, s);
-  launch_split_bf16(h->W, h->Whi, h->Wlo, (long long)mat, s);
   launch_flows(h->W, n, h->ldw, h->O, h->D, s);
   launch_total_flow(h->W, n, h->ldw, h->d_dscratch, h->d_total, s);
   CK(cudaMemcpyAsync(&h->total_flow, h->d_total, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -379,6 +379,12 @@ int create_common(usaphmp_s* h, const float* W, const float* C, bool dev, cudaSt
   CK(cudaStreamSynchronize(s));
   if (*h->h_status & kStatusBadValue) return fail(USAPHMP_EINVAL, "W or C has a negative or non-finite entry");
   h->symmetric = (*h->h_bad == 0) ? 1 : 0;
+  // symmetric C: every hub-to-hub table (direct or hub paths) is symmetric,
+  // so the tensor-core evaluator takes the folded, upper-triangular U
+  if (h->symmetric)
+    launch_split_bf16_upper(h->W, h->Whi, h->Wlo, n, h->ldw, s);
+  else
+    launch_split_bf16(h->W, h->Whi, h->Wlo, (long long)mat, s);
   if (!h->symmetric) {
     CK(dalloc(&h->CTbuf, mat));
     CK(cudaMemsetAsync(h->CTbuf, 0, mat * sizeof(float), s));
@@ -718,6 +724,17 @@ int usaphmp_autotune(usaphmp_t h, int32_t reps, const char* cache_path, usaphmp_
 int usaphmp_get_params(usaphmp_t h, usaphmp_params* prm) {
   if (!h || !prm) return fail(USAPHMP_EINVAL, "NULL argument");
   *prm = h->prm;
+  return USAPHMP_OK;
+}
+
+int usaphmp_get_info(usaphmp_t h, usaphmp_info* info) {
+  if (!h || !info) return fail(USAPHMP_EINVAL, "NULL argument");
+  info->n = h->n;
+  info->p = h->p;
+  info->ldw = h->ldw;
+  info->ns = h->ns;
+  info->c_symmetric = h->symmetric;
+  info->tc_folded = h->symmetric;
   return USAPHMP_OK;
 }
 

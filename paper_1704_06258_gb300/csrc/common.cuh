@@ -3,7 +3,8 @@
 // Layouts (row-major throughout):
 //   W, C          fp32  [n][ldw]   ldw = n rounded up to 8, zero padding
 //   CT            fp32  [n][ldw]   C transposed (aliases C when C is symmetric)
-//   Whi, Wlo      bf16  [n][ldw]   W = Whi + Wlo + O(2^-17 |W|)
+//   Whi, Wlo      bf16  [n][ldw]   W = Whi + Wlo + O(2^-17 |W|); for symmetric C
+//                                  the same split of U = W + W^T folded onto j >= i
 //   O, D          fp32  [n]        originating / destined flow (§3)
 //   mask          u32   [B][nw]    hub mask H of §4.1, bit i%32 of word i/32
 //   hubs          i32   [B][p]     open hubs in ascending node order
@@ -65,6 +66,10 @@ struct DevInst {
   const float* D;
   const __nv_bfloat16* Whi;
   const __nv_bfloat16* Wlo;
+  // 1: Whi/Wlo hold the split of U (W + W^T folded above the diagonal, W_ii
+  // on it, 0 below), valid when every hub-to-hub table is symmetric; the
+  // tensor-core evaluator then skips the K blocks left of the diagonal.
+  int wtri;
 };
 
 // A population of B chromosomes and its evaluation buffers.

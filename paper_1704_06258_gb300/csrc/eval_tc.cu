@@ -9,6 +9,10 @@
 //   * W enters as two bf16 operands, W = Whi + Wlo + O(2^-17 |W|), loaded by
 //     TMA with the 128-byte swizzle; both are multiplied by the same one-hot
 //     operand and accumulated into one fp32 TMEM tile (tcgen05.mma, kind::f16);
+//   * when C is symmetric every Chub_b is symmetric, the pairs (i, j) and
+//     (j, i) share one factor, and W is replaced by U (W + W^T folded onto
+//     j > i, W_ii on the diagonal, 0 below): row block m then needs only the
+//     K blocks from column 128 m on, about half of the MMAs;
 //   * the one-hot operand is never stored in global memory: producer warps
 //     expand it from the u8 slot codes straight into shared memory, in the
 //     same swizzled K-major layout;
@@ -189,6 +193,19 @@ __device__ __forceinline__ TileRef decode_tile(const TaskParam& tp, int g, const
   return r;
 }
 
+// The tile a CTA takes in round r of the persistent loop: tiles rG .. rG+G-1
+// go to CTAs 0 .. G-1, and with `snake` to CTAs G-1 .. 0 in odd rounds, so
+// that over the rounds every CTA gets an even share of tiles sorted by cost
+// (row-block-major tiles of a folded W, whose K loops shorten with m).
+__device__ __forceinline__ int tile_of_round(int r, bool snake) {
+  const int G = gridDim.x, c = blockIdx.x;
+  return r * G + ((snake && (r & 1)) ? G - 1 - c : c);
+}
+
+// First K block of row block m: with the folded U (zero left of the
+// diagonal) the blocks left of column 128 m add nothing.
+__device__ __forceinline__ int k_begin(const Task& T, int m) { return T.in.wtri ? (m * BM) / BK : 0; }
+
 // 0x80 in every byte of x that is zero, 0 elsewhere (no carry crosses a
 // byte: each byte's low 7 bits + 0x7F stays below 0x100).
 __device__ __forceinline__ uint32_t zero_byte_flags(uint32_t x) {
@@ -305,10 +322,86 @@ __device__ __forceinline__ void epi_chromosomes(const EpiArgs& a) {
   }
 }
 
+// epi_chromosomes for p <= LM (16, 24 or 32), software-pipelined over the
+// chromosomes: the TMEM loads of chromosome c + 1 are in flight while
+// chromosome c is summed (two register buffers of LM columns; every wait::ld
+// finds only the loads it waits for outstanding).  Same arithmetic, same
+// order.
+template <int WID, int LM>
+__device__ __forceinline__ void epi_issue(const EpiArgs& a, int c, uint32_t (&v)[LM]) {
+  const uint32_t ta = a.taddr + (uint32_t)(c * a.p);
+#pragma unroll
+  for (int l = 0; l < LM; l += WID) {
+    if (l < a.p) {
+      if constexpr (WID == 4)
+        ptx::tmem_ld_32x4(ta + l, v[l], v[l + 1], v[l + 2], v[l + 3]);
+      else if constexpr (WID == 2)
+        ptx::tmem_ld_32x2(ta + l, v[l], v[l + 1]);
+      else
+        ptx::tmem_ld_32x1(ta + l, v[l]);
+    }
+  }
+}
+
+template <int LM>
+__device__ __forceinline__ void epi_finish(const EpiArgs& a, int c, const uint32_t (&v)[LM]) {
+  const int p = a.p;
+  const int sr = !a.rvalid ? 0
+                 : a.use_tbl ? min((int)a.tbl[c * 32 + a.lane], p - 1)
+                             : min((int)__ldg(a.slot + (long long)c * a.ns + a.row), p - 1);
+  const float* frow = a.fbase + c * a.cst + sr * a.hst;
+  float acc = 0.f;
+#pragma unroll
+  for (int q = 0; q < LM / 4; ++q) {
+    if (4 * q < p) {
+      const float4 t = *reinterpret_cast<const float4*>(frow + 4 * q);
+      acc = fmaf(__uint_as_float(v[4 * q]), t.x, acc);
+      if (4 * q + 1 < p) acc = fmaf(__uint_as_float(v[4 * q + 1]), t.y, acc);
+      if (4 * q + 2 < p) acc = fmaf(__uint_as_float(v[4 * q + 2]), t.z, acc);
+      if (4 * q + 3 < p) acc = fmaf(__uint_as_float(v[4 * q + 3]), t.w, acc);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (a.lane == 0) a.out[c] = acc * kOneHotInv;
+}
+
+template <int WID, int LM>
+__device__ __forceinline__ void epi_chromosomes_pipe(const EpiArgs& a) {
+  if (a.cb >= a.ce) return;
+  uint32_t va[LM], vb[LM];
+#pragma unroll
+  for (int l = 0; l < LM; ++l) va[l] = vb[l] = 0u;
+  epi_issue<WID, LM>(a, a.cb, va);
+  int c = a.cb;
+  for (; c + 1 < a.ce; c += 2) {
+    ptx::tmem_ld_wait_n<LM>(va);
+    epi_issue<WID, LM>(a, c + 1, vb);
+    epi_finish<LM>(a, c, va);
+    ptx::tmem_ld_wait_n<LM>(vb);
+    if (c + 2 < a.ce) epi_issue<WID, LM>(a, c + 2, va);
+    epi_finish<LM>(a, c + 1, vb);
+  }
+  if (c < a.ce) {
+    ptx::tmem_ld_wait_n<LM>(va);
+    epi_finish<LM>(a, c, va);
+  }
+}
+
+template <int LM>
+__device__ __forceinline__ void epi_pipe_width(const EpiArgs& a) {
+  if ((a.p & 3) == 0)
+    epi_chromosomes_pipe<4, LM>(a);
+  else if ((a.p & 1) == 0)
+    epi_chromosomes_pipe<2, LM>(a);
+  else
+    epi_chromosomes_pipe<1, LM>(a);
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(kThreads, 1)
-    k_eval_tc(const __grid_constant__ TaskParam tp, int total_tiles, uint32_t* status, const Lay L) {
+    k_eval_tc(const __grid_constant__ TaskParam tp, int total_tiles, uint32_t* status, const Lay L, int snake) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uint32_t raw = ptx::smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -351,11 +444,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     int it = 0;
     Ring ring(STAGES);
     bool ok = true;
-    for (int g = blockIdx.x; g < total_tiles && ok; g += gridDim.x) {
+    for (int rd = 0, g = tile_of_round(0, snake); g < total_tiles && ok; g = tile_of_round(++rd, snake)) {
       const TileRef tr = decode_tile(tp, g, L);
       const Task& T = task_at(tp, tr.task);
       const int nk = (T.in.n + BK - 1) / BK;
-      for (int kb = 0; kb < nk; ++kb, ++it, ring.next()) {
+      for (int kb = k_begin(T, tr.m); kb < nk; ++kb, ++it, ring.next()) {
         const int s = ring.s;
         if (!(ok = wait_one(bars.empty(s), ring.ph ^ 1u, abort_flag, status))) break;
         const uint32_t a_hi = base + s * STAGE_BYTES;
@@ -371,7 +464,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     int tl = 0;
     Ring ring(STAGES);
     bool ok = true;
-    for (int g = blockIdx.x; g < total_tiles && ok; g += gridDim.x, ++tl) {
+    for (int rd = 0, g = tile_of_round(0, snake); g < total_tiles && ok; g = tile_of_round(++rd, snake), ++tl) {
       const TileRef tr = decode_tile(tp, g, L);
       const Task& T = task_at(tp, tr.task);
       const int p = T.in.p;
@@ -379,12 +472,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int nchrom = min(geo.cpt, T.pop.B - tr.nb * geo.cpt);
       const uint32_t idesc = ptx::idesc_bf16_f32(BM, round_up(nchrom * p, 16));
       const int nk = (T.in.n + BK - 1) / BK;
+      const int kb0 = k_begin(T, tr.m);
       const int buf = tl & 1;
       const uint32_t use = (uint32_t)(tl >> 1);
       if (!(ok = wait_one(bars.tempty(buf), (use & 1u) ^ 1u, abort_flag, status))) break;
       ptx::tc_fence_after();
       const uint32_t d = tmem + (uint32_t)(buf * L.ntile);
-      for (int kb = 0; kb < nk; ++kb, ring.next()) {
+      for (int kb = kb0; kb < nk; ++kb, ring.next()) {
         const int s = ring.s;
         if (!(ok = wait_one(bars.full_tma(s), ring.ph, abort_flag, status))) break;
         if (!(ok = wait_one(bars.full_oh(s), ring.ph, abort_flag, status))) break;
@@ -393,7 +487,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int k = 0; k < BK / 16; ++k) {
           const uint64_t bdesc = ptx::sw128_desc(bt + 32 * k);
-          ptx::mma_bf16(d, ptx::sw128_desc(a_hi + 32 * k), bdesc, idesc, (kb | k) != 0);
+          ptx::mma_bf16(d, ptx::sw128_desc(a_hi + 32 * k), bdesc, idesc, (kb != kb0 || k != 0) ? 1u : 0u);
           ptx::mma_bf16(d, ptx::sw128_desc(a_lo + 32 * k), bdesc, idesc, 1u);
         }
         ptx::tc_commit(bars.empty(s));
@@ -408,7 +502,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t* tbl = sm + L.tbl_off + quarter * (kTblChrom * 32);
     const float* slab = reinterpret_cast<const float*>(sm + L.slab_off);
     int tl = 0;
-    for (int g = blockIdx.x; g < total_tiles; g += gridDim.x, ++tl) {
+    for (int rd = 0, g = tile_of_round(0, snake); g < total_tiles; g = tile_of_round(++rd, snake), ++tl) {
       const TileRef tr = decode_tile(tp, g, L);
       const Task& T = task_at(tp, tr.task);
       const int n = T.in.n, p = T.in.p, ns = T.in.ns, B = T.pop.B;
@@ -462,12 +556,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       // one code path per TMEM load width (the widest that keeps every
       // column offset c*p + l aligned)
       const EpiArgs ea{taddr, cb, ce, p, hst, cst, ns, row, lane, rvalid, use_tbl, tbl, slot, fbase, out};
-      if ((p & 3) == 0)
+      if (p <= 16) {
+        epi_pipe_width<16>(ea);
+      } else if (p <= 24) {
+        epi_pipe_width<24>(ea);
+      } else if ((p & 3) == 0) {
         epi_chromosomes<4>(ea);
-      else if ((p & 1) == 0)
+      } else if ((p & 1) == 0) {
         epi_chromosomes<2>(ea);
-      else
+      } else {
         epi_chromosomes<1>(ea);
+      }
       // every accumulator read of this warp has completed: release the buffer
       ptx::tc_fence_before();
       ptx::mbar_arrive(bars.tempty(buf));
@@ -479,7 +578,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int r = threadIdx.x - 32 * kProdWarp0;
     Ring ring(STAGES);
     bool ok = true;
-    for (int g = blockIdx.x; g < total_tiles && ok; g += gridDim.x) {
+    for (int rd = 0, g = tile_of_round(0, snake); g < total_tiles && ok; g = tile_of_round(++rd, snake)) {
       const TileRef tr = decode_tile(tp, g, L);
       const Task& T = task_at(tp, tr.task);
       const int n = T.in.n, p = T.in.p, ns = T.in.ns, B = T.pop.B;
@@ -488,6 +587,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int nchrom = min(geo.cpt, B - b0);
       const int nmma = round_up(nchrom * p, 16);
       const int nk = (n + BK - 1) / BK;
+      const int kb0 = k_begin(T, tr.m);
       const bool valid = r < nchrom * p;   // rows in [nchrom*p, nmma) are zero
       const bool write = r < nmma;
       const bool small = p <= 63;
@@ -499,8 +599,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
       // slot codes of the next K block are loaded one block ahead
       uint4 n0 = zero4, n1 = zero4, n2 = zero4, n3 = zero4;
-      if (valid) { n0 = __ldg(src); n1 = __ldg(src + 1); n2 = __ldg(src + 2); n3 = __ldg(src + 3); }
-      for (int kb = 0; kb < nk; ++kb, ring.next()) {
+      if (valid) {
+        const uint4* f = src + kb0 * (BK / 16);
+        n0 = __ldg(f); n1 = __ldg(f + 1); n2 = __ldg(f + 2); n3 = __ldg(f + 3);
+      }
+      for (int kb = kb0; kb < nk; ++kb, ring.next()) {
         const uint4 q0 = n0, q1 = n1, q2 = n2, q3 = n3;
         if (valid && kb + 1 < nk) {
           const uint4* nx = src + (kb + 1) * (BK / 16);
@@ -569,8 +672,10 @@ void launch_eval_tc(const TaskSet& ts, int num_sms, uint32_t* status, cudaStream
   }
   const int total = tp.bo.o[ts.count];
   if (total == 0) return;
+  int snake = 0;
+  for (int k = 0; k < ts.count; ++k) snake |= ts.h[k].in.wtri;
   const int grid = total < num_sms ? total : num_sms;
-  k_eval_tc<<<grid, kThreads, kSmemBytes, s>>>(tp, total, status, L);
+  k_eval_tc<<<grid, kThreads, kSmemBytes, s>>>(tp, total, status, L, snake);
 }
 
 // Self-test of the bounded waits: the warps of one block wait on an mbarrier

@@ -33,6 +33,35 @@ __global__ void k_split_bf16(const float* __restrict__ W, __nv_bfloat16* __restr
   }
 }
 
+// The same split of U, the pairs (i, j) and (j, i) folded onto j > i:
+// U[i][j] = W[i][j] + W[j][i] for j > i, U[i][i] = W[i][i], 0 below the
+// diagonal and in the padding columns.  When every hub-to-hub cost table is
+// symmetric, sum_ij W[i][j] Chub[s(i)][s(j)] = sum_ij U[i][j] Chub[s(i)][s(j)].
+// 32 x 32 tiles: tile (bx, by) of W and its mirror tile (by, bx) through
+// shared memory, so that both reads are coalesced.
+__global__ void k_split_bf16_upper(const float* __restrict__ W, __nv_bfloat16* __restrict__ Uhi,
+                                   __nv_bfloat16* __restrict__ Ulo, int n, int ldw) {
+  __shared__ float mir[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = bx + r, j = by + threadIdx.x;  // mirror tile: rows bx.., columns by..
+    mir[r][threadIdx.x] = (i < n && j < n) ? W[(long long)i * ldw + j] : 0.f;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = by + r, j = bx + threadIdx.x;
+    if (i >= n || j >= ldw) continue;
+    float u = 0.f;
+    if (j < n) {
+      const float w = W[(long long)i * ldw + j];
+      u = j > i ? w + mir[threadIdx.x][r] : (j == i ? w : 0.f);
+    }
+    const __nv_bfloat16 hi = __float2bfloat16_rn(u);
+    Uhi[(long long)i * ldw + j] = hi;
+    Ulo[(long long)i * ldw + j] = __float2bfloat16_rn(u - __bfloat162float(hi));
+  }
+}
+
 // O_i = sum_j W[i][j] (one block per row), fp64 accumulation, fp32 result.
 __global__ void k_row_flows(const float* __restrict__ W, int n, int ldw, float* __restrict__ O) {
   __shared__ double red[32];
@@ -162,6 +191,12 @@ void launch_check_values(const float* W, const float* C, int n, int ldw, uint32_
 
 void launch_split_bf16(const float* W, __nv_bfloat16* Whi, __nv_bfloat16* Wlo, long long total, cudaStream_t s) {
   k_split_bf16<<<grid_for(total, 256), 256, 0, s>>>(W, Whi, Wlo, total);
+}
+
+void launch_split_bf16_upper(const float* W, __nv_bfloat16* Uhi, __nv_bfloat16* Ulo, int n, int ldw,
+                             cudaStream_t s) {
+  dim3 grid((ldw + 31) / 32, (n + 31) / 32), block(32, 8);
+  k_split_bf16_upper<<<grid, block, 0, s>>>(W, Uhi, Ulo, n, ldw);
 }
 
 void launch_total_flow(const float* W, int n, int ldw, double* rows, double* out, cudaStream_t s) {

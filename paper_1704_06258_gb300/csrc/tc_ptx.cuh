@@ -139,6 +139,15 @@ __device__ __forceinline__ void tmem_ld_32x4(uint32_t taddr, uint32_t& r0, uint3
                : "r"(taddr));
 }
 
+// wait::ld, then the first N registers of r pass through empty asm
+// statements that depend on it, so that no use of them moves above the wait.
+template <int N>
+__device__ __forceinline__ void tmem_ld_wait_n(uint32_t* r) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < N; ++i) asm volatile("" : "+r"(r[i]));
+}
+
 __device__ __forceinline__ void tmem_ld_wait32(uint32_t* r) {
   asm volatile("tcgen05.wait::ld.sync.aligned;"
                : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),

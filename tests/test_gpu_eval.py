@@ -25,6 +25,14 @@ def asym_instance(seed, n, p):
     return synth.Instance(f"asym{n}", n, p, W, C)
 
 
+def self_flow_instance(seed, n, p):
+    """Symmetric C with self-flows W_ii > 0 (the folded operand keeps W_ii on its diagonal)."""
+    inst = synth.urand200(seed=seed, n=n, p=p)
+    W = inst.W.copy()
+    np.fill_diagonal(W, np.random.default_rng(seed).uniform(1, 20, n).astype(np.float32))
+    return synth.Instance(f"selfflow{n}", n, p, W, inst.C)
+
+
 CASES = {
     "tiny_n10_p3": lambda: synth.tiny(),
     "n2_p1": lambda: synth.tiny(seed=5, n=2, p=1),
@@ -41,6 +49,9 @@ CASES = {
     "n240_p226_plain_smem_edge": lambda: synth.urand200(seed=84, n=240, p=226),
     "n300_p255_max": lambda: synth.urand200(seed=85, n=300, p=255),
     "asym_n150_p6": lambda: asym_instance(80, 150, 6),
+    "asym_n333_p7_ragged": lambda: asym_instance(86, 333, 7),
+    "asym_n300_p63": lambda: asym_instance(87, 300, 63),
+    "selfflow_n333_p9": lambda: self_flow_instance(88, 333, 9),
 }
 
 
@@ -216,3 +227,12 @@ def test_misaligned_slot_buffers_are_refused():
             with pytest.raises(UsaphmpError) as e:
                 call()
             assert e.value.name == "EINVAL" and "aligned" in str(e.value)
+
+
+def test_folded_operand_follows_symmetry():
+    """The tensor-core operand is folded exactly when C is symmetric."""
+    for inst, folded in ((synth.urand200(seed=90, n=70, p=4), 1), (asym_instance(91, 70, 4), 0)):
+        with Instance.from_instance(inst) as gi:
+            info = gi.info()
+            assert (info["c_symmetric"], info["tc_folded"]) == (folded, folded)
+            assert (info["n"], info["p"], info["ns"]) == (inst.n, inst.p, gi.ns)
