@@ -93,6 +93,7 @@ struct usaphmp_s {
   float* W = nullptr;
   float* C = nullptr;
   float* CTbuf = nullptr;
+  float* Ufold = nullptr;   // fp32 folded W (symmetric C): the plain evaluator's operand
   float* O = nullptr;
   float* D = nullptr;
   __nv_bfloat16* Whi = nullptr;
@@ -161,6 +162,7 @@ DevInst inst_of(const usaphmp_s* h) {
   in.W = h->W; in.C = h->C; in.CT = h->symmetric ? h->C : h->CTbuf;
   in.O = h->O; in.D = h->D; in.Whi = h->Whi; in.Wlo = h->Wlo;
   in.wtri = h->symmetric;
+  in.Ufold = h->symmetric ? h->Ufold : nullptr;
   return in;
 }
 
@@ -381,9 +383,10 @@ int create_common(usaphmp_s* h, const float* W, const float* C, bool dev, cudaSt
   h->symmetric = (*h->h_bad == 0) ? 1 : 0;
   // symmetric C: every hub-to-hub table (direct or hub paths) is symmetric,
   // so the tensor-core evaluator takes the folded, upper-triangular U
-  if (h->symmetric)
-    launch_split_bf16_upper(h->W, h->Whi, h->Wlo, n, h->ldw, s);
-  else
+  if (h->symmetric) {
+    CK(dalloc(&h->Ufold, mat));
+    launch_split_bf16_upper(h->W, h->Whi, h->Wlo, h->Ufold, n, h->ldw, s);
+  } else
     launch_split_bf16(h->W, h->Whi, h->Wlo, (long long)mat, s);
   if (!h->symmetric) {
     CK(dalloc(&h->CTbuf, mat));
@@ -574,7 +577,7 @@ void usaphmp_destroy(usaphmp_t h) {
   if (h->graph_stream) cudaStreamDestroy(h->graph_stream);
   for (int k = 0; k < 6; ++k)
     if (h->prof_ev[k]) cudaEventDestroy(h->prof_ev[k]);
-  dfree(h->W); dfree(h->C); dfree(h->CTbuf); dfree(h->O); dfree(h->D); dfree(h->Whi); dfree(h->Wlo);
+  dfree(h->W); dfree(h->C); dfree(h->CTbuf); dfree(h->Ufold); dfree(h->O); dfree(h->D); dfree(h->Whi); dfree(h->Wlo);
   if (h->tmaps) cudaFree(h->tmaps);
   dfree(h->d_status); dfree(h->d_bad); dfree(h->d_dscratch); dfree(h->d_cost); dfree(h->d_rpart);
   dfree(h->d_dist64); dfree(h->d_total); dfree(h->d_ls); dfree(h->d_ls_count); dfree(h->d_WT); dfree(h->d_OD64);

@@ -70,6 +70,7 @@ struct DevInst {
   // on it, 0 below), valid when every hub-to-hub table is symmetric; the
   // tensor-core evaluator then skips the K blocks left of the diagonal.
   int wtri;
+  const float* Ufold;  // the same U in fp32 [n][ldw] (symmetric C), else nullptr
 };
 
 // A population of B chromosomes and its evaluation buffers.

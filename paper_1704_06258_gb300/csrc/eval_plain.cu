@@ -6,6 +6,9 @@
 // thread owns 4 consecutive columns, keeps their slot codes (as table
 // offsets) in registers and streams the rows of W once for all KB
 // chromosomes: per (pair, chromosome) one shared-memory gather and one FMA.
+// For symmetric C the rows of W are those of the folded U = W + W^T on and
+// above the diagonal (0 below): each pair (i, j), (j, i) costs one gather,
+// and a thread's column chunk stops at its diagonal row.
 // Partial sums go to part[row_split][b]; the reduction kernel adds them in a
 // fixed order.  Rows are summed in chunks of 32 before joining the running
 // sum, which keeps the fp32 error near (32 + n/32) ulp instead of n ulp.
@@ -20,9 +23,9 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__host__ __device__ inline int plain_tpr(int ldw) {
-  // threads per row: enough to cover ldw/4 float4 columns, power of two
-  int need = ldw / 4, t = 32;
+__host__ __device__ inline int plain_tpr(int need) {
+  // threads per row: enough to cover `need` column chunks, power of two
+  int t = 32;
   while (t < need && t < kThreads) t <<= 1;
   return t;
 }
@@ -126,10 +129,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_plain(const __grid_constan
 
   const int chunk = (n + nrs - 1) / nrs;
   const int r0 = rs * chunk, r1 = min(n, r0 + chunk);
-  const int tpr = plain_tpr(ldw);
+  // Folded operand (symmetric C): U is zero below the diagonal, so column
+  // chunk j0..j0+3 needs rows up to j0+3 only; a thread takes a chunk and its
+  // mirror (cols4 - 1 - chunk), which together span n rows.
+  const bool fold = !gtab && T.in.Ufold != nullptr;
+  const float* __restrict__ Wm = fold ? T.in.Ufold : W;
+  const int cols4 = ldw / 4;
+  const int nchunk = fold ? (cols4 + 1) / 2 : cols4;
+  const int tpr = plain_tpr(nchunk);
   const int G = kThreads / tpr;
   const int grp = threadIdx.x / tpr, c4 = threadIdx.x - grp * tpr;
-  const int cols4 = ldw / 4;
 
   float acc[KB];
 #pragma unroll
@@ -138,8 +147,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_plain(const __grid_constan
     acc[0] = plain_global_sum(W, T.pop.chub + (long long)b0 * chub_cstride(p), sl, n, ldw, chub_hstride(p), r0, r1,
                               tpr, G, grp, c4);
 
-  for (int cb = c4; !gtab && cb < cols4; cb += tpr) {
+  for (int cp = c4; !gtab && cp < nchunk; cp += tpr)
+  for (int side = 0; side < (fold ? 2 : 1); ++side) {
+    const int cb = side == 0 ? cp : cols4 - 1 - cp;
+    if (side == 1 && cb <= cp) break;  // the middle chunk of an odd count: once
     const int j0 = cb * 4;
+    const int rend = fold ? min(r1, j0 + 4) : r1;
     int coff[KB][4];
 #pragma unroll
     for (int bb = 0; bb < KB; ++bb)
@@ -148,11 +161,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_plain(const __grid_constan
         const int j = j0 + c;
         coff[bb][c] = bb * pp + ((j < n) ? (int)sl[j * KB + bb] : 0);
       }
-    for (int i = r0 + grp; i < r1; i += 32 * G) {
+    for (int i = r0 + grp; i < rend; i += 32 * G) {
       float part[KB];
 #pragma unroll
       for (int bb = 0; bb < KB; ++bb) part[bb] = 0.f;
-      const int iend = min(r1, i + 32 * G);
+      const int iend = min(rend, i + 32 * G);
       // rows ascending; the W loads of four rows are issued before their sums
       auto row_sum = [&](const float4& w, int ii) {
         const unsigned long long codes = node_codes<KB>(sl + ii * KB);
@@ -171,11 +184,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_plain(const __grid_constan
       for (; ii + 3 * G < iend; ii += 4 * G) {
         float4 w[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) w[u] = __ldg(reinterpret_cast<const float4*>(W + (long long)(ii + u * G) * ldw + j0));
+        for (int u = 0; u < 4; ++u) w[u] = __ldg(reinterpret_cast<const float4*>(Wm + (long long)(ii + u * G) * ldw + j0));
 #pragma unroll
         for (int u = 0; u < 4; ++u) row_sum(w[u], ii + u * G);
       }
-      for (; ii < iend; ii += G) row_sum(__ldg(reinterpret_cast<const float4*>(W + (long long)ii * ldw + j0)), ii);
+      for (; ii < iend; ii += G) row_sum(__ldg(reinterpret_cast<const float4*>(Wm + (long long)ii * ldw + j0)), ii);
 #pragma unroll
       for (int bb = 0; bb < KB; ++bb) acc[bb] += part[bb];
     }

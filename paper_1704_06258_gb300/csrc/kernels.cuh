@@ -64,7 +64,7 @@ struct NvtxRange {
 // setup.cu
 void launch_check_values(const float* W, const float* C, int n, int ldw, uint32_t* status, cudaStream_t s);
 void launch_split_bf16(const float* W, __nv_bfloat16* Whi, __nv_bfloat16* Wlo, long long total, cudaStream_t s);
-void launch_split_bf16_upper(const float* W, __nv_bfloat16* Uhi, __nv_bfloat16* Ulo, int n, int ldw,
+void launch_split_bf16_upper(const float* W, __nv_bfloat16* Uhi, __nv_bfloat16* Ulo, float* Uf, int n, int ldw,
                              cudaStream_t s);
 void launch_flows(const float* W, int n, int ldw, float* O, float* D, cudaStream_t s);
 // *out = sum of all W entries in fp64 (rows: n doubles of scratch).

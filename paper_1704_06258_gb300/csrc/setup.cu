@@ -40,7 +40,7 @@ __global__ void k_split_bf16(const float* __restrict__ W, __nv_bfloat16* __restr
 // 32 x 32 tiles: tile (bx, by) of W and its mirror tile (by, bx) through
 // shared memory, so that both reads are coalesced.
 __global__ void k_split_bf16_upper(const float* __restrict__ W, __nv_bfloat16* __restrict__ Uhi,
-                                   __nv_bfloat16* __restrict__ Ulo, int n, int ldw) {
+                                   __nv_bfloat16* __restrict__ Ulo, float* __restrict__ Uf, int n, int ldw) {
   __shared__ float mir[32][33];
   const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
@@ -59,6 +59,7 @@ __global__ void k_split_bf16_upper(const float* __restrict__ W, __nv_bfloat16* _
     const __nv_bfloat16 hi = __float2bfloat16_rn(u);
     Uhi[(long long)i * ldw + j] = hi;
     Ulo[(long long)i * ldw + j] = __float2bfloat16_rn(u - __bfloat162float(hi));
+    Uf[(long long)i * ldw + j] = u;
   }
 }
 
@@ -193,10 +194,10 @@ void launch_split_bf16(const float* W, __nv_bfloat16* Whi, __nv_bfloat16* Wlo, l
   k_split_bf16<<<grid_for(total, 256), 256, 0, s>>>(W, Whi, Wlo, total);
 }
 
-void launch_split_bf16_upper(const float* W, __nv_bfloat16* Uhi, __nv_bfloat16* Ulo, int n, int ldw,
+void launch_split_bf16_upper(const float* W, __nv_bfloat16* Uhi, __nv_bfloat16* Ulo, float* Uf, int n, int ldw,
                              cudaStream_t s) {
   dim3 grid((ldw + 31) / 32, (n + 31) / 32), block(32, 8);
-  k_split_bf16_upper<<<grid, block, 0, s>>>(W, Uhi, Ulo, n, ldw);
+  k_split_bf16_upper<<<grid, block, 0, s>>>(W, Uhi, Ulo, Uf, n, ldw);
 }
 
 void launch_total_flow(const float* W, int n, int ldw, double* rows, double* out, cudaStream_t s) {
