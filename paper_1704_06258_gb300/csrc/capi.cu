@@ -147,6 +147,8 @@ struct usaphmp_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   cudaStream_t graph_stream = nullptr;
+  cudaStream_t copy_stream = nullptr;          // usaphmp_eval: input copies in chunks
+  cudaEvent_t chunk_ev[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t prof_ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
@@ -575,6 +577,9 @@ void usaphmp_destroy(usaphmp_t h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   drop_graph(h);
   if (h->graph_stream) cudaStreamDestroy(h->graph_stream);
+  for (cudaEvent_t& ev : h->chunk_ev)
+    if (ev) cudaEventDestroy(ev);
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   for (int k = 0; k < 6; ++k)
     if (h->prof_ev[k]) cudaEventDestroy(h->prof_ev[k]);
   dfree(h->W); dfree(h->C); dfree(h->CTbuf); dfree(h->Ufold); dfree(h->O); dfree(h->D); dfree(h->Whi); dfree(h->Wlo);
@@ -768,17 +773,56 @@ int usaphmp_eval(usaphmp_t h, int32_t B, const int32_t* hubs, const int32_t* S, 
     CK(cudaMallocHost(&h->h_fit_out, sizeof(float) * B));
     h->in_cap = B;
   }
+  // The inputs arrive in K chunks on a copy stream; the canonical form and
+  // the access terms of chunk k run as soon as it has landed, overlapping the
+  // copies of the later chunks; the transfer term then runs once over all B
+  // (the tensor-core kernel is most efficient on the whole population).
+  const int K = B >= 2048 ? 4 : 1;   // smaller calls lose more to the extra launches than they gain
+  if (K > 1 && !h->copy_stream) {
+    CK(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+    for (cudaEvent_t& ev : h->chunk_ev) CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  }
+  cudaStream_t cs = K > 1 ? h->copy_stream : s;
   // every return below happens after the copies from the caller's memory
-  // have finished (they are ordered before the final synchronisation of s)
+  // have finished (both streams are synchronised)
   auto finish = [&](int rc) {
+    cudaStreamSynchronize(cs);
     cudaStreamSynchronize(s);
     return rc;
   };
-  cudaError_t e = cudaMemcpyAsync(h->d_hubs_in, hubs, sizeof(int32_t) * B * h->p, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_S_in, S, sizeof(int32_t) * B * h->n, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return finish(cuda_fail(e, "usaphmp_eval input copies"));
-  int rc = enqueue_eval_canonical(h, B, h->d_hubs_in, h->d_S_in, h->d_fit_out, s);
-  if (rc != USAPHMP_OK) return finish(rc);
+  int rc = ensure_pop(h, h->ev, B);
+  if (rc != USAPHMP_OK) return rc;
+  if ((rc = reset_status(h, s)) != USAPHMP_OK) return finish(rc);
+  PopBuf full = popbuf(h, h->ev, B);
+  full.fit = h->d_fit_out;
+  full.out_scale = (float)output_scale(h);
+  const int cst = chub_cstride(h->p);
+  for (int k = 0; k < K; ++k) {
+    const int c0 = (int)((long long)B * k / K), c1 = (int)((long long)B * (k + 1) / K), nb = c1 - c0;
+    cudaError_t e = cudaMemcpyAsync(h->d_hubs_in + (size_t)c0 * h->p, hubs + (size_t)c0 * h->p,
+                                    sizeof(int32_t) * nb * h->p, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->d_S_in + (size_t)c0 * h->n, S + (size_t)c0 * h->n, sizeof(int32_t) * nb * h->n,
+                          cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess && K > 1) e = cudaEventRecord(h->chunk_ev[k], cs);
+    if (e == cudaSuccess && K > 1) e = cudaStreamWaitEvent(s, h->chunk_ev[k], 0);
+    if (e != cudaSuccess) return finish(cuda_fail(e, "usaphmp_eval input copies"));
+    launch_canon(h->d_hubs_in + (size_t)c0 * h->p, h->d_S_in + (size_t)c0 * h->n, nb, h->n, h->p, h->ns,
+                 h->ev.hubs + (size_t)c0 * h->p, h->ev.slot + (size_t)c0 * h->ns, h->d_status, h->d_bad, s, c0);
+    PopBuf pc = full;
+    pc.B = nb;
+    pc.hubs += (size_t)c0 * h->p;
+    pc.slot += (size_t)c0 * h->ns;
+    pc.t12 += c0;
+    pc.chub += (size_t)c0 * cst;
+    const Task tc = make_task(h, pc);
+    TaskSet ts{nullptr, &tc, 1};
+    launch_alloc(ts, false, use_tc(h), s);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return finish(cuda_fail(e, "usaphmp_eval chunk launch"));
+  }
+  if ((rc = run_transfer(h, make_task(h, full), s)) != USAPHMP_OK) return finish(rc);
+  cudaError_t e;
   e = cudaMemcpyAsync(h->h_fit_out, h->d_fit_out, sizeof(float) * B, cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return finish(cuda_fail(e, "usaphmp_eval fitness copy"));
   if ((rc = check_status(h, s, "usaphmp_eval")) != USAPHMP_OK) return rc;   // one synchronisation
