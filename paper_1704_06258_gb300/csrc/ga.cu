@@ -91,10 +91,13 @@ __device__ int kth_node(const uint32_t* mw, int nw, int n, uint32_t k, bool clos
     if (k < base + total) {
       const uint32_t ball = __ballot_sync(0xffffffffu, base + incl > k);
       const int L = __ffs(ball) - 1;
-      uint32_t ww = __shfl_sync(0xffffffffu, w, L);
+      const uint32_t ww = __shfl_sync(0xffffffffu, w, L);
       const uint32_t before = __shfl_sync(0xffffffffu, incl - cnt, L);
-      for (uint32_t kk = k - base - before; kk; --kk) ww &= ww - 1u;
-      return (c0 + L) * 32 + (__ffs(ww) - 1);
+      // the (k - base - before)-th set bit of ww: lane b holds bit b and
+      // counts the set bits below it
+      const uint32_t kk = k - base - before;
+      const bool hit = ((ww >> lane) & 1u) && (uint32_t)__popc(ww & ((1u << lane) - 1u)) == kk;
+      return (c0 + L) * 32 + (__ffs(__ballot_sync(0xffffffffu, hit)) - 1);
     }
     base += total;
   }
