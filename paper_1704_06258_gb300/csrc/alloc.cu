@@ -32,6 +32,8 @@ template <bool kNearest>
 __global__ void __launch_bounds__(kAllocThreads) k_alloc(const __grid_constant__ TaskParam tp, int with_chub) {
   __shared__ int hs[kMaxP];
   __shared__ float red[32];
+  pdl_wait();
+  pdl_allow_next();
   const int t = task_of(tp.bo, blockIdx.x);
   const Task& T = task_at(tp, t);
   const int b = blockIdx.x - tp.bo.o[t];
@@ -238,9 +240,9 @@ void launch_alloc(const TaskSet& ts, bool nearest, bool with_chub, cudaStream_t 
     if (ts.h[t].in.routing && p * p <= kFwSmemEntries) smem = std::max(smem, (size_t)p * p * sizeof(float));
   }
   if (nearest)
-    k_alloc<true><<<blocks, kAllocThreads, smem, s>>>(tp, with_chub ? 1 : 0);
+    launch_pdl(k_alloc<true>, blocks, kAllocThreads, smem, s, tp, with_chub ? 1 : 0);
   else
-    k_alloc<false><<<blocks, kAllocThreads, smem, s>>>(tp, with_chub ? 1 : 0);
+    launch_pdl(k_alloc<false>, blocks, kAllocThreads, smem, s, tp, with_chub ? 1 : 0);
 }
 
 }  // namespace usaphmp

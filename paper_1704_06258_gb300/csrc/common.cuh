@@ -122,6 +122,15 @@ __device__ inline int find_task(const int* off, int ntasks, int blk) {
   return t;
 }
 
+// Programmatic dependent launch: a kernel launched with launch_pdl may start
+// while the previous kernel of its stream is finishing; pdl_wait() returns
+// once that kernel has completed and its writes are visible (at once when
+// the launch has no such dependency), so every kernel calls it before its
+// first global access.  pdl_allow_next() lets the next kernel launch once
+// every block of this one has started.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_allow_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ inline float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

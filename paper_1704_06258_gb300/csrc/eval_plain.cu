@@ -88,6 +88,8 @@ template <int KB>
 __global__ void __launch_bounds__(kThreads, 2) k_eval_plain(const __grid_constant__ TaskParam tp) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ float red[kThreads / 32];
+  pdl_wait();
+  pdl_allow_next();
   const int t = task_of(tp.bo, blockIdx.x);
   const Task& T = task_at(tp, t);
   const int n = T.in.n, p = T.in.p, ldw = T.in.ldw, ns = T.in.ns, B = T.pop.B;
@@ -227,7 +229,7 @@ void launch_eval_plain(const TaskSet& ts, cudaStream_t s) {
   switch (kb) {
 #define USAPHMP_PLAIN_CASE(K)                                 \
   case K:                                                     \
-    k_eval_plain<K><<<blocks, kThreads, smem, s>>>(tp);       \
+    launch_pdl(k_eval_plain<K>, blocks, kThreads, smem, s, tp); \
     break;
     USAPHMP_PLAIN_CASE(8)
     USAPHMP_PLAIN_CASE(4)

@@ -438,6 +438,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   ptx::tc_fence_after();
   const uint32_t tmem = *tmem_holder;
+  // barriers and TMEM are set up: now wait for the allocation kernel's output
+  pdl_wait();
+  pdl_allow_next();
 
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------------------ TMA producer
@@ -675,7 +678,7 @@ void launch_eval_tc(const TaskSet& ts, int num_sms, uint32_t* status, cudaStream
   int snake = 0;
   for (int k = 0; k < ts.count; ++k) snake |= ts.h[k].in.wtri;
   const int grid = total < num_sms ? total : num_sms;
-  k_eval_tc<<<grid, kThreads, kSmemBytes, s>>>(tp, total, status, L, snake);
+  launch_pdl(k_eval_tc, grid, kThreads, kSmemBytes, s, tp, total, status, L, snake);
 }
 
 // Self-test of the bounded waits: the warps of one block wait on an mbarrier

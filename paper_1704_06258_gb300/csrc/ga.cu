@@ -138,6 +138,8 @@ __device__ void correct(uint32_t* mw, int nw, int n, int p, Draws& d) {
 
 __global__ void __launch_bounds__(64) k_children(const __grid_constant__ TaskParam tp) {
   extern __shared__ uint32_t msm[];
+  pdl_wait();
+  pdl_allow_next();
   const int t = task_of(tp.bo, blockIdx.x);
   const Task& T = task_at(tp, t);
   const int n = T.in.n, p = T.in.p, nw = T.in.nw;
@@ -302,6 +304,8 @@ __global__ void __launch_bounds__(128) k_reduce_select(const __grid_constant__ T
   __shared__ float sv[4];
   __shared__ int si[4];
   __shared__ int s_last, s_rb;
+  pdl_wait();
+  pdl_allow_next();
   const int t = task_of(tp.bo, blockIdx.x);
   const Task& T = task_at(tp, t);
   const int r = blockIdx.x - tp.bo.o[t];
@@ -398,7 +402,7 @@ void launch_reduce_select(const TaskSet& ts, cudaStream_t s) {
   for (int t = 0; t < ts.count; ++t) tp.bo.o[t + 1] = tp.bo.o[t] + ts.h[t].ga.R;
   const int blocks = tp.bo.o[ts.count];
   if (blocks == 0) return;
-  k_reduce_select<<<blocks, 128, 0, s>>>(tp);
+  launch_pdl(k_reduce_select, blocks, 128, 0, s, tp);
 }
 
 // Start state: every ancestor and the best-ever = the initial solution.
@@ -425,7 +429,7 @@ void launch_children(const TaskSet& ts, cudaStream_t s) {
   }
   const int blocks = tp.bo.o[ts.count];
   if (blocks == 0) return;
-  k_children<<<blocks, 64, 4 * nw * sizeof(uint32_t), s>>>(tp);
+  launch_pdl(k_children, blocks, 64, 4 * nw * sizeof(uint32_t), s, tp);
 }
 
 void launch_select(const TaskSet& ts, cudaStream_t s) {

@@ -1,5 +1,6 @@
 // Host-side launchers of the library's kernels (all stream-ordered, no sync).
 #pragma once
+#include <utility>
 #include <nvtx3/nvToolsExt.h>
 #include <string>
 
@@ -8,6 +9,23 @@
 namespace usaphmp {
 
 constexpr int kMaxTasks = 64;
+
+// Launch with programmatic stream serialisation (see pdl_wait in common.cuh).
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Block ranges of the tasks of one launch: task t owns global blocks
 // [o[t], o[t+1]).  Passed by value so that a captured graph keeps it.

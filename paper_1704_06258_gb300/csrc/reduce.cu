@@ -9,6 +9,8 @@
 namespace usaphmp {
 
 __global__ void k_reduce(const __grid_constant__ TaskParam tp) {
+  pdl_wait();
+  pdl_allow_next();
   const int t = task_of(tp.bo, blockIdx.x);
   const Task& T = task_at(tp, t);
   const int b = (blockIdx.x - tp.bo.o[t]) * blockDim.x + threadIdx.x;
@@ -23,7 +25,7 @@ void launch_reduce(const TaskSet& ts, cudaStream_t s) {
   for (int t = 0; t < ts.count; ++t) tp.bo.o[t + 1] = tp.bo.o[t] + (ts.h[t].pop.B + 127) / 128;
   const int blocks = tp.bo.o[ts.count];
   if (blocks == 0) return;
-  k_reduce<<<blocks, 128, 0, s>>>(tp);
+  launch_pdl(k_reduce, blocks, 128, 0, s, tp);
 }
 
 }  // namespace usaphmp
