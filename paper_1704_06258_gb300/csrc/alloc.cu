@@ -62,9 +62,12 @@ __global__ void __launch_bounds__(kAllocThreads) k_alloc(const __grid_constant__
     // ascending hub order per node (lowest hub on ties).  Hubs serve
     // themselves: a node that is a hub takes its own slot afterwards.
     __shared__ uint32_t hub_bits[kMaxN / 32];
-    for (int w = threadIdx.x; w < (n + 31) / 32; w += blockDim.x) hub_bits[w] = 0u;
-    __syncthreads();
-    for (int k = threadIdx.x; k < p; k += blockDim.x) atomicOr(&hub_bits[hs[k] >> 5], 1u << (hs[k] & 31));
+    for (int w = threadIdx.x; w < (n + 31) / 32; w += blockDim.x) {
+      uint32_t bits = 0u;
+      for (int k = 0; k < p; ++k)
+        if ((hs[k] >> 5) == w) bits |= 1u << (hs[k] & 31);
+      hub_bits[w] = bits;
+    }
     __syncthreads();
     const int n4 = (n + 3) >> 2;
     for (int g = threadIdx.x; g < n4; g += blockDim.x) {
@@ -92,21 +95,24 @@ __global__ void __launch_bounds__(kAllocThreads) k_alloc(const __grid_constant__
         if (v.w < best.w) { best.w = v.w; b3 = l; }
       }
       // one node of the group: own slot for a hub, access terms, slot code
-      auto finish = [&](int i, int bl, float cih) -> uint32_t {
+      const float4 o4 = __ldg(reinterpret_cast<const float4*>(O) + g);
+      const float4 d4 = __ldg(reinterpret_cast<const float4*>(D) + g);
+      const uint32_t hw = hub_bits[i0 >> 5];  // the group's four nodes share one bitmap word
+      auto finish = [&](int i, int bl, float cih, float oi, float di) -> uint32_t {
         if (i >= n) return (uint32_t)kSlotPad;
-        if ((hub_bits[i >> 5] >> (i & 31)) & 1u) {
+        if ((hw >> (i & 31)) & 1u) {
           for (int q = 0; q < p; ++q)
             if (hs[q] == i) bl = q;
           cih = CT[(long long)i * ldw + i];
         }
         const float chi_i = sym ? cih : C[(long long)hs[bl] * ldw + i];  // C[h(i), i]
-        acc += access_term(chi, O[i], cih, delta, D[i], chi_i);
+        acc += access_term(chi, oi, cih, delta, di, chi_i);
         return (uint32_t)bl;
       };
-      const uint32_t s0 = finish(i0, b0, best.x);
-      const uint32_t s1 = finish(i0 + 1, b1, best.y);
-      const uint32_t s2 = finish(i0 + 2, b2, best.z);
-      const uint32_t s3 = finish(i0 + 3, b3, best.w);
+      const uint32_t s0 = finish(i0, b0, best.x, o4.x, d4.x);
+      const uint32_t s1 = finish(i0 + 1, b1, best.y, o4.y, d4.y);
+      const uint32_t s2 = finish(i0 + 2, b2, best.z, o4.z, d4.z);
+      const uint32_t s3 = finish(i0 + 3, b3, best.w, o4.w, d4.w);
       const uint32_t packed = s0 | (s1 << 8) | (s2 << 16) | (s3 << 24);
       *reinterpret_cast<uint32_t*>(slot + i0) = packed;
     }
@@ -132,12 +138,15 @@ __global__ void __launch_bounds__(kAllocThreads) k_alloc(const __grid_constant__
         cih[k] = CT[(long long)hs[bl[k]] * ldw + i];                       // C[i, h(i)]
         chi_i[k] = sym ? cih[k] : C[(long long)hs[bl[k]] * ldw + i];      // C[h(i), i]
       }
+      const float4 o4 = __ldg(reinterpret_cast<const float4*>(O) + g);
+      const float4 d4 = __ldg(reinterpret_cast<const float4*>(D) + g);
+      const float ok[4] = {o4.x, o4.y, o4.z, o4.w}, dk[4] = {d4.x, d4.y, d4.z, d4.w};
       uint32_t packed = 0u;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int i = i0 + k;
         if (i < n) {
-          acc += access_term(chi, O[i], cih[k], delta, D[i], chi_i[k]);
+          acc += access_term(chi, ok[k], cih[k], delta, dk[k], chi_i[k]);
           packed |= (uint32_t)bl[k] << (8 * k);
         } else {
           packed |= (uint32_t)kSlotPad << (8 * k);

@@ -353,8 +353,8 @@ int create_common(usaphmp_s* h, const float* W, const float* C, bool dev, cudaSt
   const size_t mat = (size_t)n * h->ldw;
   CK(dalloc(&h->W, mat));
   CK(dalloc(&h->C, mat));
-  CK(dalloc(&h->O, n));
-  CK(dalloc(&h->D, n));
+  CK(dalloc(&h->O, h->ns));   // padded to ns: the allocation kernel reads four nodes at a time
+  CK(dalloc(&h->D, h->ns));
   CK(dalloc(&h->Whi, mat));
   CK(dalloc(&h->Wlo, mat));
   CK(dalloc(&h->d_status, 1));
@@ -371,6 +371,8 @@ int create_common(usaphmp_s* h, const float* W, const float* C, bool dev, cudaSt
   CK(cudaMemcpy2DAsync(h->C, h->ldw * sizeof(float), C, n * sizeof(float), n * sizeof(float), n, kind, s));
   RET(reset_status(h, s));
   launch_check_values(h->W, h->C, n, h->ldw, h->d_status, s);
+  CK(cudaMemsetAsync(h->O, 0, sizeof(float) * h->ns, s));
+  CK(cudaMemsetAsync(h->D, 0, sizeof(float) * h->ns, s));
   launch_flows(h->W, n, h->ldw, h->O, h->D, s);
   launch_total_flow(h->W, n, h->ldw, h->d_dscratch, h->d_total, s);
   CK(cudaMemcpyAsync(&h->total_flow, h->d_total, sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -5,7 +5,7 @@
 //   CT            fp32  [n][ldw]   C transposed (aliases C when C is symmetric)
 //   Whi, Wlo      bf16  [n][ldw]   W = Whi + Wlo + O(2^-17 |W|); for symmetric C
 //                                  the same split of U = W + W^T folded onto j >= i
-//   O, D          fp32  [n]        originating / destined flow (§3)
+//   O, D          fp32  [ns]       originating / destined flow (§3), zero past n
 //   mask          u32   [B][nw]    hub mask H of §4.1, bit i%32 of word i/32
 //   hubs          i32   [B][p]     open hubs in ascending node order
 //   slot          u8    [B][ns]    rank in `hubs` of the hub serving node i;
