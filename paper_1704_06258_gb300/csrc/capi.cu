@@ -553,7 +553,8 @@ size_t usaphmp::handle_device_bytes(int n, int p, int R, int P) {
   const size_t ldw = round_up(n, 8), ns = round_up(n, 64), nw = (n + 31) / 32;
   const size_t B = (size_t)R * P;
   const size_t mat = (size_t)n * ldw;
-  size_t bytes = 3 * mat * 4 + 2 * mat * 2 + 4 * (size_t)n * 4 + 256;   // W, C, CT, Whi, Wlo, O, D, misc
+  // W, C and either CT (asymmetric C) or the fp32 folded U (symmetric C); Whi, Wlo; O, D (ns each); misc
+  size_t bytes = 3 * mat * 4 + 2 * mat * 2 + 2 * ns * 4 + 2 * (size_t)n * 4 + 256;
   const size_t rows = std::max((size_t)tc_part_rows(n), (size_t)plain_rows(n, (int)B));
   const size_t per_chrom = nw * 4 + (size_t)p * 4 + ns + 8 + (size_t)chub_cstride(p) * 4 + rows * 4;
   bytes += (B + 1) * per_chrom + (size_t)R * (nw * 4 + 4) + 3 * nw * 4 + 1024;
