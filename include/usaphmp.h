@@ -353,7 +353,9 @@ int usaphmp_get_tile(usaphmp_t h, usaphmp_tile* tile);
 int usaphmp_autotune(usaphmp_t h, int32_t reps, const char* cache_path, usaphmp_tile* chosen,
                      double* chosen_ms, double* default_ms, int32_t* from_cache);
 
-/* The autotuner's JSON cache, host only (no GPU needed).  A file holds
+/* The autotuner's JSON cache, host only (no GPU needed).  usaphmp_autotune
+ * keys it by the device name, followed by " (folded operand)" for instances
+ * whose C is symmetric.  A file holds
  *   {"format": "usaphmp-tile-cache-1", "entries": [{"device": "...",
  *    "n_blocks": ceil(n/128), "p": p, "B_pow2": B rounded up to a power of
  *    two, "ntile": ..., "stages": ..., "raster": ..., "ms": ...}, ...]}.

@@ -668,9 +668,11 @@ int usaphmp_autotune(usaphmp_t h, int32_t reps, const char* cache_path, usaphmp_
   CK(cudaGetDevice(&dev_id));
   cudaDeviceProp prop;
   CK(cudaGetDeviceProperties(&prop, dev_id));
+  // the folded operand runs other K loops than the full W: separate buckets
+  const std::string device = std::string(prop.name) + (h->symmetric ? " (folded operand)" : "");
   if (cache_path) {
     usaphmp_tile t{};
-    const int r = usaphmp_tile_cache_lookup(cache_path, prop.name, h->n, h->p, B, &t, nullptr);
+    const int r = usaphmp_tile_cache_lookup(cache_path, device.c_str(), h->n, h->p, B, &t, nullptr);
     if (r < 0) return r;
     if (r == 1 && usaphmp_set_tile(h, &t) == USAPHMP_OK) {
       if (from_cache) *from_cache = 1;
@@ -725,7 +727,7 @@ int usaphmp_autotune(usaphmp_t h, int32_t reps, const char* cache_path, usaphmp_
   drop_graph(h);
   if (cache_path) {
     const usaphmp_tile t{best.ntile, best.stages, best.raster};
-    RET(usaphmp_tile_cache_store(cache_path, prop.name, h->n, h->p, B, &t, best_ms));
+    RET(usaphmp_tile_cache_store(cache_path, device.c_str(), h->n, h->p, B, &t, best_ms));
   }
   if (chosen_ms) *chosen_ms = best_ms;
   if (default_ms) *default_ms = dflt_ms;

@@ -87,3 +87,20 @@ def test_autotune_on_the_plain_path_keeps_the_shape(tmp_path):
         assert {k: got[k] for k in ("ntile", "stages", "raster")} == {"ntile": 256, "stages": 3, "raster": 0}
         assert got["ms"] == 0.0 and not got["from_cache"]
     assert not (tmp_path / "tiles.json").exists()
+
+
+def test_cache_buckets_separate_folded_and_full_operands(tmp_path):
+    """A shape tuned on a symmetric instance (folded operand) is not reused for
+    an asymmetric instance of the same size, and the reverse."""
+    cache = str(tmp_path / "tiles.json")
+    sym = synth.urand200(seed=17, n=260, p=9)
+    C = sym.C.copy()
+    C[0, 1] += 1.0          # one asymmetric pair: the full W operand
+    asym = synth.Instance("asym260", sym.n, sym.p, sym.W, C)
+    for inst in (sym, asym):
+        with Instance.from_instance(inst) as gi:
+            gi.set_params(islands=4, island_size=32, path=PATH_SPLIT_BF16)
+            got = gi.autotune(reps=2, cache=cache)
+            assert not got["from_cache"]
+    devices = sorted(e["device"] for e in json.load(open(cache))["entries"])
+    assert len(devices) == 2 and devices[1] == devices[0] + " (folded operand)"
