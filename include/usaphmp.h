@@ -245,8 +245,10 @@ int usaphmp_ga_load(usaphmp_t h, const void* buf, int64_t bytes, void* stream);
  *   slot  u8  [B][ns] (device, in/out): rank in hubs of each node's hub,
  *         a valid single allocation on entry (every hub in its own slot)
  *   moves, sweeps  i32 [B] out (device, may be NULL): moves made, sweeps run
- * Allocates B * (2*n*p + p*p) doubles of scratch for the call and
- * synchronises `stream` before returning. */
+ * Scratch: B * (2*n*p + p*(p|1)) doubles, kept by the handle and grown when
+ * a call needs more; the first call also makes W transposed and the fp64
+ * flow sums (n*n floats + 2n doubles).  Synchronises `stream` before
+ * returning. */
 int usaphmp_local_search_dev(usaphmp_t h, int32_t B, const int32_t* hubs, uint8_t* slot, int32_t max_sweeps,
                              int32_t* moves, int32_t* sweeps, void* stream);
 

@@ -114,6 +114,8 @@ struct usaphmp_s {
   double* d_dist64 = nullptr;  // p*p fp64 hub-path table of the returned solution (hub-path routing)
   double* d_total = nullptr;   // sum of W, fp64 (device)
   double* d_ls = nullptr;      // local-search scratch of the returned solution
+  double* d_ls_batch = nullptr;  // usaphmp_local_search_dev scratch (grows, kept)
+  size_t ls_batch_cap = 0;
   float* d_WT = nullptr;       // local search: W transposed and fp64 flow sums [O; D]
   double* d_OD64 = nullptr;    //   (made on first use)
   double* d_part64 = nullptr;  // fp64 reference path: per-chromosome partial sums,
@@ -190,7 +192,7 @@ int ensure_fp64(usaphmp_s* h, int B) {
 // flow sums), made on first use.
 int ensure_ls(usaphmp_s* h, cudaStream_t s) {
   if (h->d_WT && h->d_OD64) return USAPHMP_OK;
-  dfree(h->d_WT); dfree(h->d_OD64);
+  dfree(h->d_WT); dfree(h->d_OD64); dfree(h->d_ls_batch);
   float* wt = nullptr;
   double* od = nullptr;
   CK(dalloc(&wt, (size_t)h->n * h->ldw));
@@ -933,14 +935,17 @@ int usaphmp_local_search_dev(usaphmp_t h, int32_t B, const int32_t* hubs, uint8_
   if (max_sweeps < 1) return fail(USAPHMP_EINVAL, "max_sweeps must be >= 1");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   RET(ensure_ls(h, s));
-  double* scratch = nullptr;
-  CK(dalloc(&scratch, (size_t)B * local_search_scratch_doubles(h->n, h->p)));
-  launch_local_search(inst_of(h), h->d_WT, h->d_OD64, B, hubs, slot, max_sweeps, scratch, moves, sweeps, s);
-  cudaError_t e = cudaGetLastError();
-  cudaError_t e2 = cudaStreamSynchronize(s);
-  cudaFree(scratch);
-  CK(e);
-  CK(e2);
+  const size_t need = (size_t)B * local_search_scratch_doubles(h->n, h->p);
+  if (h->ls_batch_cap < need) {
+    CK(cudaStreamSynchronize(s));  // a previous call's kernels may still use the old scratch
+    dfree(h->d_ls_batch);
+    h->ls_batch_cap = 0;
+    CK(dalloc(&h->d_ls_batch, need));
+    h->ls_batch_cap = need;
+  }
+  launch_local_search(inst_of(h), h->d_WT, h->d_OD64, B, hubs, slot, max_sweeps, h->d_ls_batch, moves, sweeps, s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
   return USAPHMP_OK;
 }
 
