@@ -33,15 +33,51 @@ UNIT = "evals/s"
 WORKLOAD = "clustered n=1000 p=20, population 4096 (64 islands x 64), one GA generation per step"
 N, P_HUBS, ISLANDS, ISLAND = 1000, 20, 64, 64
 L2_FLUSH_BYTES = 512 << 20
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_eval_tc launch on this
-# workload, from the ncu capture summarised in profiles/k_eval_tc_clustered_n1000_p20.md
-# (None whenever the kernel has changed since that capture).
-K_EVAL_TC_DRAM_BYTES = 13385984
-# the same for one k_alloc launch (profiles/k_alloc_clustered_n1000_p20.md)
-K_ALLOC_DRAM_BYTES = 4373248
-# sm__pipe_tensor_cycles_active (fraction of peak, elapsed) of that k_eval_tc capture
-K_EVAL_TC_TENSOR_ACTIVE = 0.585
+CSRC = os.path.join(ROOT, "paper_1704_06258_gb300", "csrc")
+# ncu counters of one launch of a kernel on this workload, valid only for
+# the kernel sources they were captured on: each entry names its source files and their sha256 at capture
+# time, and the line reports the counters only while the files still hash
+# to it (null otherwise: the kernel changed since the capture).
+PROFILED = {
+    "k_eval_tc": {"files": ["eval_tc.cu", "tc_ptx.cuh", "common.cuh"], "sha256": None,
+                  "dram_bytes": None, "tensor_pipe_active": None},
+    "k_alloc": {"files": ["alloc.cu", "common.cuh"], "sha256": None, "dram_bytes": None},
+}
 REF_MEMBERS = 16
+
+
+def source_sha256(files):
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled(kernel, key):
+    """The captured counter `key` of `kernel`, or None when its sources changed."""
+    e = PROFILED[kernel]
+    return e.get(key) if e["sha256"] and e["sha256"] == source_sha256(e["files"]) else None
+
+
+def l2_read_gbs(reps=20, mb=16, times=64):
+    """L2 read bandwidth as a plain reduction reaches it: a 16 MB buffer (far
+    below the 126 MB L2) read `times` times per launch through a stride-0
+    view, bytes read / time, CUDA events around `reps` launches after a
+    warm-up."""
+    import torch
+    a = torch.ones((mb << 20) // 4, dtype=torch.float32, device="cuda")
+    view = a.view(1, -1).expand(times, -1)
+    for _ in range(3):
+        view.sum(dim=1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        view.sum(dim=1)
+    e1.record()
+    torch.cuda.synchronize()
+    return float(a.numel()) * 4 * times * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
 
 
 def load_peaks():
@@ -56,7 +92,7 @@ class ClockSampler:
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,utilization.gpu")
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
@@ -87,24 +123,35 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
+        """Median SM clock over the samples taken under load (GPU utilisation
+        above 0) and over all samples, the maximum clock, and every throttle
+        reason seen active."""
+        sm, sm_load, mx, reasons = [], [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
+                mhz = float(f[1])
                 mx = float(f[2])
             except ValueError:
                 continue
+            sm.append(mhz)
+            try:
+                if float(f[9]) > 0:
+                    sm_load.append(mhz)
+            except ValueError:
+                pass
             for name, v in zip(names, f[5:9]):
                 if v.lower() == "active":
                     reasons.add(name)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": statistics.median(sm_load) if sm_load else statistics.median(sm),
+                "sm_mhz_all_samples": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm), "samples_under_load": len(sm_load),
+                "window": "from before the warm-up of the timed generations to the end of the e2e leg"}
 
 
 from paper_1704_06258_gb300.dist import barrier, max_over_ranks, weak_scaling_value  # noqa: E402
@@ -501,13 +548,18 @@ def run_ours(args):
             tile = dict(gi.get_tile(), fixed=True)
         else:
             tile = gi.autotune(reps=20)  # tile shape of the TC kernel, chosen before any timing
+        # clocks are sampled from before the warm-up of the timed generations
+        # to the end of the e2e leg (the timed region alone lasts a few ms)
         with ClockSampler(local) as clk:
             gmean, gmedian, wall = graph_generations(gi, args.steps, args.warmup, flush, stream, world)
-        # per-stage breakdown from an eager run with events between the kernels
-        split, _, res = timed_generations(gi, max(3, min(args.steps, 400)), args.warmup, flush, stream, world)
-        e2e = None if only_split else e2e_eval(gi, inst, steps=max(3, min(50, args.steps // 20)), warmup=1)
+            # per-stage breakdown from an eager run with events between the kernels
+            split, _, res = timed_generations(gi, max(3, min(args.steps, 400)), args.warmup, flush, stream, world)
+            e2e = None if only_split else e2e_eval(gi, inst, steps=max(3, min(50, args.steps // 20)), warmup=1)
+            if clk.proc is not None:
+                time.sleep(0.45)         # at least two samples of the 200 ms sampler
         gi_solve_s = None if only_split else gi.solve(1000, 2024)["ms"] * 1e-3
         rel_err = None if only_split else rel_error_sample(gi, inst)
+    l2_gbs = l2_read_gbs() if world == 1 else None
     large = large_n_leg(20, 3, flush, stream) if (not only_split and world == 1 and args.large) else None
     routed = routing_leg(200, 3, flush, stream) if (not only_split and world == 1 and args.large) else None
     sweep = factor_sweep() if (not only_split and world == 1 and args.large) else None
@@ -524,15 +576,17 @@ def run_ours(args):
     flops_per_launch = tc_flops(N, P_HUBS, B, folded)
     k1_ms = split["transfer"]
     achieved = flops_per_launch / (k1_ms * 1e-3) / 1e12
-    if peaks and peaks.get("bf16_tflops_sustained"):
-        peak, peak_src = peaks["bf16_tflops_sustained"], "measured bf16 sustained (MEASURED_PEAKS.json)"
+    # k_eval_tc is a 0.14 ms kernel timed alone between events: the burst peak
+    if peaks and peaks.get("bf16_tflops"):
+        peak, peak_src = peaks["bf16_tflops"], "measured bf16 burst (MEASURED_PEAKS.json)"
     else:
-        peak, peak_src = 1700.0, "fallback sustained bf16"
+        peak, peak_src = 1900.0, "fallback bf16 burst"
+    # the method's own arithmetic: n^2 pair multiply-adds per evaluation
+    method_flops = 2.0 * N * N * B
     cpu1 = cpu_baseline(inst) if (world == 1 and not args.no_cpu and rank == 0) else None
     a_bytes = alloc_bytes(N, P_HUBS, B)
     a_ms = split["allocation"]
-    hbm = (peaks or {}).get("hbm_gbs") or 6800.0
-    hbm_src = "measured HBM copy (MEASURED_PEAKS.json)" if (peaks or {}).get("hbm_gbs") else "fallback HBM"
+    clocks = clk.summary()
     if rank != 0:
         return
     line = {
@@ -548,22 +602,33 @@ def run_ours(args):
                    "tile": tile},
         "roofline": {"kernel": "k_eval_tc (transfer term)", "bound": "tensor", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": peak_src,
-                     "traffic": K_EVAL_TC_DRAM_BYTES, "flops_per_launch": flops_per_launch, "avg_launch_ms": k1_ms},
+                     "traffic": profiled("k_eval_tc", "dram_bytes"), "flops_per_launch": flops_per_launch,
+                     "flops_per_unit": flops_per_launch / B, "avg_launch_ms": k1_ms,
+                     "work": "issued one-hot GEMM work: 2 GEMMs (U_hi, U_lo) x 2 flops x p x n(n+1)/2 folded "
+                             "entries per chromosome",
+                     "method_work": {"flops_per_launch": method_flops, "flops_per_unit": 2.0 * N * N,
+                                     "achieved": method_flops / (k1_ms * 1e-3) / 1e12,
+                                     "frac": method_flops / (k1_ms * 1e-3) / 1e12 / peak,
+                                     "what": "the method's own arithmetic, n^2 pair multiply-adds per "
+                                             "evaluation, over the same launch time and peak"}},
         "roofline_gather": {"kernel": "k_alloc (nearest allocation + access terms + hub-cost tables)",
-                            "bound": "hbm", "achieved": a_bytes / (a_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-                            "frac": a_bytes / (a_ms * 1e-3) / 1e9 / hbm, "peak_source": hbm_src,
-                            "traffic": K_ALLOC_DRAM_BYTES, "bytes_per_launch": a_bytes, "avg_launch_ms": a_ms,
-                            "note": "C (4 MB) stays in L2 at n=1000, so the algorithmic bytes are L2-served; "
-                                    "see large_n for the n=6000 case where C (144 MB) exceeds L2"},
+                            "bound": "l2", "achieved": a_bytes / (a_ms * 1e-3) / 1e9, "peak": l2_gbs, "unit": "GB/s",
+                            "frac": (a_bytes / (a_ms * 1e-3) / 1e9 / l2_gbs) if l2_gbs else None,
+                            "peak_source": "measured in this run: a torch reduction reading a 16 MB "
+                                           "L2-resident buffer 64 times per launch (bytes read per second)",
+                            "traffic": profiled("k_alloc", "dram_bytes"), "bytes_per_launch": a_bytes,
+                            "avg_launch_ms": a_ms,
+                            "note": "C (4 MB) stays in L2 at n=1000: the gathers are L2 reads, not HBM traffic"},
         "cpu_baseline": cpu1,
         "cpu_baseline_all_cores": cpu_baseline_all_cores(cpu1["per_step_s"]) if cpu1 else None,
         "e2e": e2e,
         "gpu_launches": 4 * args.steps,   # children, allocation, transfer, reduce+select
-        "clocks": clk.summary(),
+        "clocks": clocks,
+        "ms_x_mhz": gmean * clocks["sm_mhz"] if clocks.get("sm_mhz") else None,
         "ms_per_step_median": gmedian,
         "ms_per_step_eager": split["generation"],   # the same generation launched eagerly with stage events
         "pair_ops_per_s": value * N * N,   # algorithmic work: n^2 pair multiply-adds per evaluation
-        "tensor_pipe_active_ncu": K_EVAL_TC_TENSOR_ACTIVE,
+        "tensor_pipe_active_ncu": profiled("k_eval_tc", "tensor_pipe_active"),
         "paper_context": paper_context(gi_solve_s),
         "stage_ms": {k: round(v, 5) for k, v in split.items() if k != "generation_median"},
         "plain_fp32": {"value": B * world / (plain_ms * 1e-3), "ms_per_step": plain_ms,

@@ -205,7 +205,6 @@ int usaphmp_select_dev(usaphmp_t h, int32_t R, int32_t P, int32_t g, const uint3
                        const float* fitness, uint32_t* anc, float* anc_fit, uint32_t* best,
                        float* best_fit, void* stream);
 
-/* FP64 objective (pair form of eq. 1) of B canonical chromosomes: cost [B]. */
 /* Island exchange for a population sharded over GPUs (§5 outer loop; the
  * caller moves the data between processes).  usaphmp_ga_islands copies the
  * current ancestors (host, [R][nw] words, bit i%32 of word i/32 = node i)
@@ -216,6 +215,13 @@ int usaphmp_select_dev(usaphmp_t h, int32_t R, int32_t P, int32_t g, const uint3
  * with n1 = 0 and call this after every n1 generations).  Both need
  * usaphmp_ga_begin first and synchronise `stream`. */
 int usaphmp_ga_islands(usaphmp_t h, uint32_t* masks, float* fit, void* stream);
+
+/* The population of the last generation run (§5): the children's hub masks
+ * (host, [R*P][nw] words, chromosome q = r*P + j of island r) and their raw
+ * fp32 fitness (host, [R*P]) as the selection saw them; before the first
+ * generation their contents are unspecified.  Either output may be NULL.
+ * Needs usaphmp_ga_begin first; synchronises `stream`. */
+int usaphmp_ga_population(usaphmp_t h, uint32_t* masks, float* fit, void* stream);
 int usaphmp_ga_merge(usaphmp_t h, const uint32_t* mask, float fit, void* stream);
 
 /* Checkpoint / resume of the GA between generations.  The state is small:
@@ -252,6 +258,15 @@ int usaphmp_ga_load(usaphmp_t h, const void* buf, int64_t bytes, void* stream);
 int usaphmp_local_search_dev(usaphmp_t h, int32_t B, const int32_t* hubs, uint8_t* slot, int32_t max_sweeps,
                              int32_t* moves, int32_t* sweeps, void* stream);
 
+/* FP64 objective of B canonical chromosomes (§3, eq. 1 in its pair form:
+ * sum_i sum_j W[i][j] (chi C[i][h(i)] + alpha T[h(i)][h(j)] + delta C[h(j)][j]),
+ * T the transfer leg of the handle's routing), every product and sum in fp64
+ * from the fp32 instance and the fp64 factors given at creation, times the
+ * handle's output scale.
+ *   hubs i32 [B][p] ascending node ids, slot u8 [B][ns] (device); cost fp64 [B]
+ *   out (device).
+ * Scratch (B * min(n, 128) doubles, and B*p*p more with hub-path routing) is
+ * allocated for the call and freed before it returns; synchronises `stream`. */
 int usaphmp_rescore_fp64_dev(usaphmp_t h, int32_t B, const int32_t* hubs, const uint8_t* slot,
                              double* cost, void* stream);
 
@@ -393,24 +408,27 @@ int usaphmp_selftest_wait_timeout(int64_t limit_ns, uint32_t* status, int64_t* e
  * memory budget or pool owned by a host application, or a latency-critical
  * loop where cudaMalloc's implicit device synchronisation is not acceptable.
  *
- * Same result as usaphmp_rescore_fp64_dev (fp64 pair form of eq. 1) without a
- * handle: every input and the output are caller device buffers, and the
- * function neither allocates nor frees anything.  Its per-block partial sums
- * go to a fixed scratch array compiled into the library: 131072 doubles
- * (1 MiB), present on every GPU that loads the library until the process
- * exits.
- *   W, C   fp32 [n][n] row-major (dense, no padding)
+ * The fp64 pair form of eq. 1, as usaphmp_rescore_fp64_dev computes it for a
+ * handle with the default routing and scale -- the transfer leg on the direct
+ * hub arc C[h(i)][h(j)] and the raw, unscaled cost -- but without a handle:
+ * every input and the output are caller device buffers, and the function
+ * neither allocates nor frees anything.  Its per-block partial sums go to a
+ * fixed scratch array compiled into the library: 131072 doubles (1 MiB),
+ * present on every GPU that loads the library until the process exits.
+ *   W, C   fp32 [n][n] row-major (dense, no padding; C need not be symmetric)
  *   hubs   i32  [B][p] ascending node ids; slot u8 [B][n] (rank in hubs of the
  *          hub serving node i); cost fp64 [B] out.
  * Sizes: 2 <= n <= 16384, 1 <= p <= min(n, 255), and B * min(n, 128) must not
  * exceed 131072 (else USAPHMP_EINVAL, nothing launched).  Enqueued on
  * `stream`, no synchronisation.
- * The first call on a device looks up the scratch array's device address on
- * the current device; make that first call before any stream capture.  All
- * calls share the one scratch array (every call rewrites the entries it reads,
- * nothing needs to start at zero), so calls whose work overlaps on the GPU --
- * on different streams or from different threads -- race and return wrong
- * costs: order them on one stream or synchronise between them. */
+ * Set-up: the scratch array's device address is looked up once per CUDA
+ * context of a device (the first call on a device, and the first call after
+ * that device's context was reset), with the device current; make that first
+ * call before any stream capture.  All calls share the one scratch array
+ * (every call rewrites the entries it reads, nothing needs to start at zero),
+ * so calls whose work overlaps on the GPU -- on different streams or from
+ * different threads -- race and return wrong costs: order them on one stream
+ * or synchronise between them. */
 int usaphmp_rescore_fp64_noalloc(int32_t n, int32_t p, int32_t B, const float* W, const float* C,
                                  double chi, double alpha, double delta, const int32_t* hubs,
                                  const uint8_t* slot, double* cost, void* stream);

@@ -95,6 +95,7 @@ _SIGS = {
     "usaphmp_debug_fail_allocations": (c_i32, [c_i32]),
     "usaphmp_selftest_wait_timeout": (c_i32, [c_i64, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(c_i64)]),
     "usaphmp_ga_islands": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
+    "usaphmp_ga_population": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
     "usaphmp_ga_state_bytes": (c_i32, [c_vp, ctypes.POINTER(c_i64)]),
     "usaphmp_ga_save": (c_i32, [c_vp, c_vp, c_i64, c_vp]),
     "usaphmp_ga_load": (c_i32, [c_vp, c_vp, c_i64, c_vp]),
@@ -345,6 +346,16 @@ class Instance:
         masks = np.empty((R, self.nw), dtype=np.uint32)
         fit = np.empty(R, dtype=np.float32)
         check(lib().usaphmp_ga_islands(self.h, _ptr(masks), _ptr(fit), stream))
+        return masks, fit
+
+    def ga_population(self, stream=0):
+        """usaphmp_ga_population: the last generation's children (masks uint32
+        [R*P, nw]) and their raw fitness (float32 [R*P])."""
+        prm = self.params
+        B = prm["islands"] * prm["island_size"]
+        masks = np.empty((B, self.nw), dtype=np.uint32)
+        fit = np.empty(B, dtype=np.float32)
+        check(lib().usaphmp_ga_population(self.h, _ptr(masks), _ptr(fit), stream))
         return masks, fit
 
     def ga_merge(self, mask, fit, stream=0):

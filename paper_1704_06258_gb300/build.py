@@ -47,7 +47,10 @@ def _compile(src, extra):
 def build(verbose=False, extra=()):
     os.makedirs(BUILD, exist_ok=True)
     srcs = sources()
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "usaphmp.h")]
+    # the library is stale when any source, the header or this script (its
+    # flags and architecture) is newer than it
+    deps = ([os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "usaphmp.h")] +
+            [os.path.abspath(__file__)])
     newest = max(os.path.getmtime(d) for d in deps)
     if os.path.exists(LIB) and os.path.getmtime(LIB) >= newest and not extra:
         return LIB

@@ -192,7 +192,7 @@ int ensure_fp64(usaphmp_s* h, int B) {
 // flow sums), made on first use.
 int ensure_ls(usaphmp_s* h, cudaStream_t s) {
   if (h->d_WT && h->d_OD64) return USAPHMP_OK;
-  dfree(h->d_WT); dfree(h->d_OD64); dfree(h->d_ls_batch);
+  dfree(h->d_WT); dfree(h->d_OD64);
   float* wt = nullptr;
   double* od = nullptr;
   CK(dalloc(&wt, (size_t)h->n * h->ldw));
@@ -591,6 +591,8 @@ void usaphmp_destroy(usaphmp_t h) {
   if (h->tmaps) cudaFree(h->tmaps);
   dfree(h->d_status); dfree(h->d_bad); dfree(h->d_dscratch); dfree(h->d_cost); dfree(h->d_rpart);
   dfree(h->d_dist64); dfree(h->d_total); dfree(h->d_ls); dfree(h->d_ls_count); dfree(h->d_WT); dfree(h->d_OD64);
+  dfree(h->d_ls_batch);
+  h->ls_batch_cap = 0;
   dfree(h->d_part64); dfree(h->d_cost64); dfree(h->d_paths64);
   if (h->h_status) cudaFreeHost(h->h_status);
   if (h->h_bad) cudaFreeHost(h->h_bad);
@@ -1180,6 +1182,18 @@ int usaphmp_ga_islands(usaphmp_t h, uint32_t* masks, float* fit, void* stream) {
   const int R = h->ga_task.ga.R;
   if (masks) CK(cudaMemcpyAsync(masks, h->anc, sizeof(uint32_t) * R * h->nw, cudaMemcpyDeviceToHost, s));
   if (fit) CK(cudaMemcpyAsync(fit, h->anc_fit, sizeof(float) * R, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return USAPHMP_OK;
+}
+
+int usaphmp_ga_population(usaphmp_t h, uint32_t* masks, float* fit, void* stream) {
+  if (!h) return fail(USAPHMP_EINVAL, "NULL handle");
+  if (!h->ga_ready) return fail(USAPHMP_EINVAL, "usaphmp_ga_begin first");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Task& t = h->ga_task;
+  const size_t B = (size_t)t.ga.R * t.ga.P;
+  if (masks) CK(cudaMemcpyAsync(masks, t.pop.mask, sizeof(uint32_t) * B * h->nw, cudaMemcpyDeviceToHost, s));
+  if (fit) CK(cudaMemcpyAsync(fit, t.pop.fit, sizeof(float) * B, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   return USAPHMP_OK;
 }

@@ -48,8 +48,9 @@ constexpr int kProdWarp0 = kEpiWarp0 + kEpiWarps;
 constexpr int kThreads = 32 * (kProdWarp0 + 8);
 constexpr uint32_t A_BYTES = BM * BK * 2;                 // 16 KB
 constexpr int kMaxStages = 4;
-constexpr int kTblChrom = 86;                              // slot-code table: u8 [4 warps][86][32 rows]
-constexpr uint32_t kTblBytes = 4 * kTblChrom * 32;
+constexpr int kTblChrom = 86;                              // chromosomes of a tile whose slot codes are tabled
+constexpr int kTblWarpChrom = kTblChrom / 2;               // per epilogue warp: u8 [8 warps][43][32 rows]
+constexpr uint32_t kTblBytes = kEpiWarps * kTblWarpChrom * 32;
 constexpr int kNumBars = 3 * kMaxStages + 7;
 constexpr uint32_t kSmemBytes = 232448;                    // dynamic shared memory of one CTA (227 KB)
 constexpr uint32_t kUsable = kSmemBytes - 1024;            // after aligning the base to 1024
@@ -283,7 +284,7 @@ __device__ __forceinline__ void epi_chromosomes(const EpiArgs& a) {
   const int p = a.p;
   for (int c = a.cb; c < a.ce; ++c) {
     const int sr = !a.rvalid ? 0
-                   : a.use_tbl ? min((int)a.tbl[c * 32 + a.lane], p - 1)
+                   : a.use_tbl ? min((int)a.tbl[(c - a.cb) * 32 + a.lane], p - 1)
                                : min((int)__ldg(a.slot + (long long)c * a.ns + a.row), p - 1);
     const float* frow = a.fbase + c * a.cst + sr * a.hst;
     float acc = 0.f;
@@ -347,7 +348,7 @@ template <int LM>
 __device__ __forceinline__ void epi_finish(const EpiArgs& a, int c, const uint32_t (&v)[LM]) {
   const int p = a.p;
   const int sr = !a.rvalid ? 0
-                 : a.use_tbl ? min((int)a.tbl[c * 32 + a.lane], p - 1)
+                 : a.use_tbl ? min((int)a.tbl[(c - a.cb) * 32 + a.lane], p - 1)
                              : min((int)__ldg(a.slot + (long long)c * a.ns + a.row), p - 1);
   const float* frow = a.fbase + c * a.cst + sr * a.hst;
   float acc = 0.f;
@@ -502,7 +503,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + kEpiWarps) {
     // --------------------------------------------------------------- epilogue
     const int quarter = warp & 3, half = (warp - kEpiWarp0) >> 2;
-    uint8_t* tbl = sm + L.tbl_off + quarter * (kTblChrom * 32);
+    // this warp's own slot-code table: rows of its chromosomes [cb, ce) of the
+    // current tile (private, so refilling it for the next tile cannot race
+    // with the other warps still reading theirs, whatever the next tile's
+    // chromosome split)
+    uint8_t* tbl = sm + L.tbl_off + (warp - kEpiWarp0) * (kTblWarpChrom * 32);
     const float* slab = reinterpret_cast<const float*>(sm + L.slab_off);
     int tl = 0;
     for (int rd = 0, g = tile_of_round(0, snake); g < total_tiles; g = tile_of_round(++rd, snake), ++tl) {
@@ -544,7 +549,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             sv[u] = (rvalid && c0 + u < ce) ? __ldg(slot + (long long)(c0 + u) * ns + row) : (uint8_t)0;
 #pragma unroll
           for (int u = 0; u < 8; ++u)
-            if (c0 + u < ce) tbl[(c0 + u) * 32 + lane] = sv[u];
+            if (c0 + u < ce) tbl[(c0 + u - cb) * 32 + lane] = sv[u];
         }
         __syncwarp();
       }

@@ -127,55 +127,137 @@ __global__ void k_transpose(const float* __restrict__ C, float* __restrict__ CT,
   }
 }
 
-// d_i = sum_j C[i][j] in fp64: the "middle node" score of §4.1.
-__global__ void k_middle_score(const float* __restrict__ C, int n, int ldw, double* __restrict__ d) {
-  __shared__ double red[32];
-  const int i = blockIdx.x;
-  double s = 0.0;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) s += (double)C[(long long)i * ldw + j];
-  s = block_sum_f64(s, red);
-  if (threadIdx.x == 0) d[i] = s;
+// d_i = sum_j C[i][j], the "middle node" score of §4.1, correctly rounded to
+// fp64: the entries are non-negative fp32 values, so each one is an integer
+// multiple of 2^-149 below 2^128 and the row sum is an exact integer count of
+// 2^-149 (under 2^292).  Every thread adds its entries' 24-bit significands,
+// shifted to their place, into nine 32-bit-aligned 64-bit digits (no digit
+// can overflow: each gets at most 2n addends below 2^32), the digits are
+// summed over the block (integer addition: exact in any order) and thread 0
+// carries them into a 320-bit integer and rounds it once, to nearest with
+// ties to even.  The score therefore does not depend on the order of the
+// entries: rows that are permutations of each other, and mathematically
+// equal sums, tie exactly, and the lower id wins as §4.1's selection asks.
+constexpr int kScoreDigits = 9;   // bit 32*k of the sum scaled by 2^149
+
+__device__ double digits_to_double(const unsigned long long (&acc)[kScoreDigits]) {
+  uint32_t limb[kScoreDigits + 1];
+  unsigned long long carry = 0;
+  for (int q = 0; q < kScoreDigits; ++q) {
+    const unsigned long long t = acc[q] + carry;
+    limb[q] = (uint32_t)t;
+    carry = t >> 32;
+  }
+  limb[kScoreDigits] = (uint32_t)carry;
+  int top = kScoreDigits;
+  while (top >= 0 && limb[top] == 0u) --top;
+  if (top < 0) return 0.0;
+  const int L = 32 * top + 32 - __clz(limb[top]);   // bit length of the integer
+  auto bit = [&](int q) -> uint32_t { return q < 0 ? 0u : (limb[q >> 5] >> (q & 31)) & 1u; };
+  unsigned long long mant = 0;                      // the leading 53 bits (zeros below bit 0)
+  for (int q = L - 1; q >= L - 53; --q) mant = (mant << 1) | bit(q);
+  int e2 = L - 1 - 149;                             // binary exponent of the leading bit
+  if (L > 53 && bit(L - 54)) {                      // round bit set: round up unless an exact tie to even
+    bool sticky = false;
+    for (int q = L - 55; q >= 0 && !sticky; --q) sticky = bit(q) != 0u;
+    if (sticky || (mant & 1ull)) {
+      if ((++mant) >> 53) {
+        mant >>= 1;
+        ++e2;
+      }
+    }
+  }
+  // normal for every sum here: -149 <= e2 <= 170
+  return __longlong_as_double((long long)(((unsigned long long)(e2 + 1023) << 52) | (mant & ((1ull << 52) - 1))));
 }
 
-// One block: the p nodes with the smallest d (lower node id on ties) become
-// the hubs of the initial solution; writes the mask and the ascending hubs.
-__global__ void k_middle_select(const double* __restrict__ d, int n, int p, int nw,
-                                uint32_t* __restrict__ mask, int32_t* __restrict__ hubs) {
-  extern __shared__ uint32_t taken[];   // nw words
-  __shared__ double bv[32];
-  __shared__ int bi[32];
-  for (int w = threadIdx.x; w < nw; w += blockDim.x) taken[w] = 0u;
-  __syncthreads();
-  for (int r = 0; r < p; ++r) {
-    double v = 1e308;
-    int idx = 0x7fffffff;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      if (taken[i >> 5] & (1u << (i & 31))) continue;
-      const double x = d[i];
-      if (x < v || (x == v && i < idx)) { v = x; idx = i; }
-    }
+__global__ void __launch_bounds__(256) k_middle_score(const float* __restrict__ C, int n, int ldw,
+                                                      double* __restrict__ d) {
+  __shared__ unsigned long long part[8][kScoreDigits];
+  const int i = blockIdx.x;
+  unsigned long long acc[kScoreDigits];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, v, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-      if (ov < v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+  for (int q = 0; q < kScoreDigits; ++q) acc[q] = 0ull;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const uint32_t bits = __float_as_uint(C[(long long)i * ldw + j]) & 0x7FFFFFFFu;   // -0.0 counts as 0
+    const uint32_t e = bits >> 23;
+    const uint32_t m = (bits & 0x7FFFFFu) | (e ? 0x800000u : 0u);
+    const uint32_t sh = e ? e - 1u : 0u;            // value = m * 2^(sh - 149)
+    const unsigned long long v = (unsigned long long)m << (sh & 31u);
+    const uint32_t k = sh >> 5, lo = (uint32_t)v, hi = (uint32_t)(v >> 32);
+#pragma unroll
+    for (int q = 0; q < kScoreDigits; ++q) {
+      acc[q] += (q == (int)k) ? lo : 0u;
+      acc[q] += (q == (int)k + 1) ? hi : 0u;
     }
-    if ((threadIdx.x & 31) == 0) { bv[threadIdx.x >> 5] = v; bi[threadIdx.x >> 5] = idx; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double bestv = bv[0];
-      int besti = bi[0];
-      for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-        if (bv[w] < bestv || (bv[w] == bestv && bi[w] < besti)) { bestv = bv[w]; besti = bi[w]; }
-      taken[besti >> 5] |= 1u << (besti & 31);
-    }
-    __syncthreads();
   }
-  for (int w = threadIdx.x; w < nw; w += blockDim.x) mask[w] = taken[w];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < kScoreDigits; ++q) {
+    unsigned long long v = acc[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) part[w][q] = v;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    int k = 0;
-    for (int i = 0; i < n && k < p; ++i)
-      if (taken[i >> 5] & (1u << (i & 31))) hubs[k++] = i;
+    unsigned long long tot[kScoreDigits];
+    for (int q = 0; q < kScoreDigits; ++q) {
+      tot[q] = 0ull;
+      for (int x = 0; x < (int)(blockDim.x >> 5); ++x) tot[q] += part[x][q];
+    }
+    d[i] = digits_to_double(tot);
+  }
+}
+
+// Middle-node hubs (§4.1): node i is a hub when fewer than p nodes precede it
+// in the order (d, node id), i.e. its rank among the n scores is below p.
+// One thread per node counts the nodes before it (scores staged through
+// shared memory); a warp covers 32 consecutive nodes, so its ballot is one
+// word of the hub mask.
+constexpr int kRankThreads = 128, kRankTile = 2048;
+
+__global__ void __launch_bounds__(kRankThreads) k_middle_rank(const double* __restrict__ d, int n, int p, int nw,
+                                                             uint32_t* __restrict__ mask) {
+  __shared__ double tile[kRankTile];
+  const int i = blockIdx.x * kRankThreads + threadIdx.x;
+  const double di = i < n ? d[i] : 0.0;
+  int rank = 0;
+  for (int j0 = 0; j0 < n; j0 += kRankTile) {
+    const int cnt = min(kRankTile, n - j0);
+    __syncthreads();
+    for (int j = threadIdx.x; j < cnt; j += kRankThreads) tile[j] = d[j0 + j];
+    __syncthreads();
+    for (int j = 0; j < cnt; ++j) {
+      const double x = tile[j];
+      rank += (x < di || (x == di && j0 + j < i)) ? 1 : 0;
+    }
+  }
+  const uint32_t word = __ballot_sync(0xffffffffu, i < n && rank < p);
+  const int wi = i >> 5;
+  if ((threadIdx.x & 31) == 0 && wi < nw) mask[wi] = word;
+}
+
+// Ascending hub list of a mask (one warp; prefix counts of the words).
+__global__ void k_mask_hubs(const uint32_t* __restrict__ mask, int nw, int32_t* __restrict__ hubs) {
+  const int lane = threadIdx.x;
+  int base = 0;
+  for (int c0 = 0; c0 < nw; c0 += 32) {
+    const int x = c0 + lane;
+    uint32_t v = x < nw ? mask[x] : 0u;
+    const int cnt = __popc(v);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    int pos = base + incl - cnt;
+    while (v) {
+      hubs[pos++] = x * 32 + (__ffs(v) - 1);
+      v &= v - 1u;
+    }
+    base += __shfl_sync(0xffffffffu, incl, 31);
   }
 }
 
@@ -223,7 +305,8 @@ void launch_middle_nodes(const float* C, int n, int ldw, int p, double* dscratch
                          int32_t* hubs, cudaStream_t s) {
   k_middle_score<<<n, 256, 0, s>>>(C, n, ldw, dscratch);
   const int nw = (n + 31) / 32;
-  k_middle_select<<<1, 1024, nw * sizeof(uint32_t), s>>>(dscratch, n, p, nw, mask, hubs);
+  k_middle_rank<<<(n + kRankThreads - 1) / kRankThreads, kRankThreads, 0, s>>>(dscratch, n, p, nw, mask);
+  k_mask_hubs<<<1, 32, 0, s>>>(mask, nw, hubs);
 }
 
 }  // namespace usaphmp

@@ -103,28 +103,36 @@ def exchange_best(fit, island, mask, islands_per_rank, world):
     return wfit, wisland, buf.cpu().numpy().view(np.uint32).copy()
 
 
-def sharded_solve(gi, generations, seed, islands_per_rank, island_size, n1, rank, world, stream=0):
+def sharded_solve(gi, generations, seed, islands_per_rank, island_size, n1, rank, world, stream=0,
+                  on_generation=None, on_merge=None):
     """One island population of world * islands_per_rank islands, this rank
     holding islands [rank * islands_per_rank, (rank + 1) * islands_per_rank)
-    of it on its GPU (an Instance).  The library runs the inner loop with its
-    own merge turned off; every n1 generations the ranks merge through
-    exchange_best.  Returns the global best (hubs, S, cost_fp64, cost_fp32)
-    on every rank; between ranks, equal best fitness goes to the lower rank."""
+    of it on its GPU (an Instance).  The library runs the generations with its
+    own merge turned off (each replayed from its CUDA graph); after every n1
+    generations the ranks merge through exchange_best.  Returns the global
+    best (hubs, S, cost_fp64, cost_fp32) on every rank; between ranks, equal
+    best fitness goes to the lower rank.
+
+    Observers (optional, for checks and tracing): on_generation(g, gi) after
+    generation g has run on this rank, before any merge; on_merge(g, wfit,
+    wisland, wmask) after the merge that follows generation g."""
     import numpy as np
     gi.set_params(islands=islands_per_rank, island_size=island_size, n1=0,
                   island_offset=rank * islands_per_rank)
     gi.ga_begin(seed, stream)
-    done = 0
-    while done < generations:
-        k = min(n1, generations - done)
-        gi.ga_run(k, stream)
-        done += k
-        if k == n1:
+    for g in range(generations):
+        gi.ga_run(1, stream)
+        if on_generation is not None:
+            on_generation(g, gi)
+        if n1 > 0 and (g + 1) % n1 == 0:
             masks, fit = gi.ga_islands(stream)
             key = np.where(np.isnan(fit), np.inf, fit)
             r = int(np.argmin(key))
-            wfit, _, wmask = exchange_best(fit[r], rank * islands_per_rank + r, masks[r], islands_per_rank, world)
+            wfit, wisland, wmask = exchange_best(fit[r], rank * islands_per_rank + r, masks[r], islands_per_rank,
+                                                 world)
             gi.ga_merge(wmask, wfit, stream)
+            if on_merge is not None:
+                on_merge(g, wfit, wisland, wmask)
     res = gi.ga_result(stream)
     return best_over_ranks(res, rank, world)
 

@@ -141,3 +141,38 @@ def test_states_from_other_parameters_are_refused():
             gi.ga_load(bytes(bad))                         # not a state
         gi.ga_load(state)
         gi.ga_run(1)
+
+
+def test_destroyed_handles_give_back_their_device_memory():
+    """A handle that ran every kind of work (GA, batch local search with its
+    kept scratch, rescoring, evaluation) returns all its device memory when it
+    is destroyed: the device's free memory after three create/run/destroy
+    cycles equals that after the first (which also loads the kernels)."""
+    import torch
+    from gpu_util import dev, stream
+    inst = synth.clustered(seed=17, n=600, p=20)
+    B, ns = 64, 640
+    hubs, S = synth.random_population(18, inst.n, inst.p, B)
+    hs = np.sort(hubs, axis=1).astype(np.int32)
+    d_hs = dev(hs)
+    d_slot = torch.empty((B, ns), dtype=torch.uint8, device="cuda")
+    d_cost = torch.empty(B, dtype=torch.float64, device="cuda")
+
+    def cycle():
+        with Instance.from_instance(inst) as gi:
+            assert gi.ns == ns
+            gi.set_params(islands=4, island_size=16)
+            gi.solve(3, 1)
+            gi.allocate_dev(B, d_hs.data_ptr(), d_slot.data_ptr(), stream())
+            gi.local_search_dev(B, d_hs.data_ptr(), d_slot.data_ptr(), 3)
+            gi.rescore_fp64_dev(B, d_hs.data_ptr(), d_slot.data_ptr(), d_cost.data_ptr(), stream())
+            assert np.isfinite(gi.eval(hubs, S)).all()
+        torch.cuda.synchronize()
+
+    cycle()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        cycle()
+    free1 = torch.cuda.mem_get_info()[0]
+    # the local-search scratch alone is B*(2np + p(p|1)) doubles = 12.5 MB per handle here
+    assert free1 >= free0 - (2 << 20), (free0 - free1) / 2**20

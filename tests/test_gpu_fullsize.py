@@ -82,3 +82,41 @@ def test_clustered1000_ga_generation_bit_exact_sampled():
     for b in np.random.default_rng(403).choice(B, 24, replace=False):
         hb = np.flatnonzero(ref[b])
         np.testing.assert_array_equal(slots[b, :inst.n], cost.slots_of(hb, cost.nearest_allocation(inst.C, hb)))
+
+
+def test_clustered1000_graph_generations_follow_the_oracle():
+    """The benchmarked path itself -- 64 islands x 64 on clustered n=1000, p=20,
+    split-bf16, generations replayed from the CUDA graph with the fused
+    reduction + selection -- one generation at a time: every child mask, the
+    ancestors and their fitness after every selection (a merge every second
+    generation) and the final best-ever against the oracle's GA fed the GPU's
+    fitness; sampled fitness against the fp64 objective."""
+    inst = synth.clustered()
+    n, p = inst.n, inst.p
+    R, P, N1, seed, G = 64, 64, 2, 4321, 3
+    B = R * P
+    rng = np.random.default_rng(404)
+    with Instance.from_instance(inst) as gi:
+        gi.set_params(islands=R, island_size=P, n1=N1, path=PATH_SPLIT_BF16, use_graph=1)
+        gi.ga_begin(seed)
+        am, af = gi.ga_islands()
+        m0 = np.isin(np.arange(n), cost.middle_nodes(inst.C, p))
+        np.testing.assert_array_equal(unpack_masks(am, n), np.tile(m0, (R, 1)))
+        assert (af == af[0]).all()
+        st = ga.State(np.tile(m0, (R, 1)), af.astype(np.float64), m0, float(af[0]))
+        for g in range(G):
+            gi.ga_run(1)
+            masks, fit = gi.ga_population()
+            children = ga.make_children(st.ancestors, seed, g, p, P)
+            np.testing.assert_array_equal(unpack_masks(masks, n), children)
+            for b in rng.choice(B, 6, replace=False):
+                h = cost.nearest_allocation(inst.C, np.flatnonzero(children[b]))
+                ref = cost.pair_cost(inst.W, inst.C, inst.chi, inst.alpha, inst.delta, h)
+                assert abs(fit[b] - ref) / ref <= TOL[PATH_SPLIT_BF16]
+            ga.select(st, children, fit.astype(np.float64), g, P, N1)
+            am, af = gi.ga_islands()
+            np.testing.assert_array_equal(unpack_masks(am, n), st.ancestors)
+            np.testing.assert_array_equal(af, st.anc_fit.astype(np.float32))
+        res = gi.ga_result()
+    np.testing.assert_array_equal(res["hubs"], np.flatnonzero(st.best))
+    assert np.float32(res["cost_fp32"]) == np.float32(st.best_fit)

@@ -29,6 +29,33 @@ def test_initial_solution_is_middle_nodes(n, p):
     np.testing.assert_array_equal(np.flatnonzero(mask), ref)
 
 
+def _lattice(side, seed=0):
+    """Nodes on a side x side unit grid: symmetric nodes have rows of C that
+    are permutations of each other, so their middle-node scores tie exactly."""
+    xy = np.stack(np.meshgrid(np.arange(side), np.arange(side), indexing="ij"), -1).reshape(-1, 2).astype(np.float64)
+    d = xy[:, None, :] - xy[None, :, :]
+    C = np.sqrt((d ** 2).sum(-1)).astype(np.float32)
+    W = np.random.default_rng(seed).uniform(0, 1, C.shape).astype(np.float32)
+    np.fill_diagonal(W, 0.0)
+    return W, C
+
+
+@pytest.mark.parametrize("side,p", [(9, 1), (9, 4), (9, 9), (12, 1), (12, 6), (12, 10)])
+def test_initial_solution_ties_on_a_lattice(side, p):
+    W, C = _lattice(side)
+    n = side * side
+    inst = synth.Instance(f"lattice{side}", n, p, W, C)
+    with Instance.from_instance(inst) as gi:
+        m = torch.zeros(gi.nw, dtype=torch.int32, device="cuda")
+        h = torch.zeros(p, dtype=torch.int32, device="cuda")
+        gi.initial_dev(m.data_ptr(), h.data_ptr(), stream())
+        hubs = host(h)
+        mask = unpack_masks(host(m).view(np.uint32)[None], n)[0]
+    ref = cost.middle_nodes(C, p)
+    np.testing.assert_array_equal(hubs, ref)
+    np.testing.assert_array_equal(np.flatnonzero(mask), ref)
+
+
 @pytest.mark.parametrize("n,p,B", [(10, 3, 16), (200, 10, 64), (333, 7, 40), (1000, 20, 24), (64, 64, 3)])
 def test_allocation_bit_exact(n, p, B):
     inst = synth.urand200(seed=n + 1, n=n, p=p) if n != 1000 else synth.clustered()

@@ -142,3 +142,75 @@ def test_search_matches_oracle_without_fp32_screen():
         ref, rs, rm = local_search(inst.W, inst.C, inst.chi, inst.alpha, inst.delta, hubs[b], starts[b], 3)
         np.testing.assert_array_equal(got[b], ref, err_msg=f"chromosome {b}")
         assert (moves[b], sweeps[b]) == (rm, rs)
+
+
+def _oracle_pool(inst):
+    """Spawned oracle workers (no CUDA state) holding the instance."""
+    import multiprocessing as mp
+    import os
+    from concurrent.futures import ProcessPoolExecutor
+
+    import oracle_workers
+    return ProcessPoolExecutor(min(16, os.cpu_count() or 1), mp_context=mp.get_context("spawn"),
+                               initializer=oracle_workers.init,
+                               initargs=(inst.W, inst.C, inst.chi, inst.alpha, inst.delta))
+
+
+def test_search_matches_oracle_at_n400():
+    """Whole searches at n = 400 against the oracle's (which evaluates every
+    candidate move as a difference of two pair-form costs): allocations,
+    moves and sweeps, from a nearest and from a random allocation."""
+    import oracle_workers
+    seed, n, p = 71, 400, 6
+    inst = heavy_tailed(seed, n, p)
+    rng = np.random.default_rng(seed)
+    hubs = np.stack([np.sort(rng.choice(n, p, replace=False)) for _ in range(2)])
+    starts = []
+    for b in range(2):
+        s = cost.nearest_allocation(inst.C, hubs[b]) if b == 0 else hubs[b][rng.integers(0, p, size=n)]
+        s = s.copy()
+        s[hubs[b]] = hubs[b]
+        starts.append(s)
+    starts = np.stack(starts)
+    with _oracle_pool(inst) as pool:
+        refs = pool.map(oracle_workers.run_local_search, [(hubs[b], starts[b], 20, "direct") for b in range(2)])
+        with Instance.from_instance(inst) as gi:
+            got, moves, sweeps, _, _ = run_gpu(gi, hubs, starts, 20)
+        refs = list(refs)
+    for b, (ref, rs, rm) in enumerate(refs):
+        np.testing.assert_array_equal(got[b], ref, err_msg=f"chromosome {b}")
+        assert (moves[b], sweeps[b]) == (rm, rs)
+    assert moves.sum() > 0
+
+
+def test_bench_size_result_is_a_local_optimum_sampled():
+    """At the bench size (clustered n = 1000, p = 20) the search's result, for
+    32 sampled spokes of each of 4 chromosomes, admits no improving single
+    reallocation by the oracle's pair-form costs, and the fp64 cost the GPU
+    returns for it equals the oracle's."""
+    import oracle_workers
+    inst = synth.clustered()
+    B, per = 4, 32
+    hubs, _ = synth.random_population(11, inst.n, inst.p, B)
+    hubs = np.sort(hubs, axis=1)
+    S = np.stack([cost.nearest_allocation(inst.C, h) for h in hubs])
+    with Instance.from_instance(inst) as gi:
+        got, moves, sweeps, d_hs, d_slot = run_gpu(gi, hubs, S, 50)
+        c = torch.empty(B, dtype=torch.float64, device="cuda")
+        gi.rescore_fp64_dev(B, d_hs.data_ptr(), d_slot.data_ptr(), c.data_ptr(), stream())
+        gpu_cost = host(c)
+    assert (sweeps < 50).all() and (moves > 0).any()
+    rng = np.random.default_rng(12)
+    jobs = []
+    for b in range(B):
+        spokes = np.setdiff1d(np.arange(inst.n), hubs[b])
+        for i in rng.choice(spokes, per, replace=False):
+            jobs.append((got[b], int(i), hubs[b]))
+    with _oracle_pool(inst) as pool:
+        out = list(pool.map(oracle_workers.single_move_changes, jobs, chunksize=4))
+    for k, (changes, base) in enumerate(out):
+        b = k // per
+        assert gpu_cost[b] == pytest.approx(base, rel=1e-12)
+        # a change the two fp64 sums cannot tell from zero is no improvement
+        worst = min(d for _, d in changes)
+        assert worst >= -1e-13 * base, (b, jobs[k][1], worst)

@@ -132,3 +132,54 @@ def test_invalid_request_fails_alone():
                 break
         assert isinstance(res[tb], UsaphmpError) and res[tb].name == "EINVAL"
         assert isinstance(res[tg], dict)
+
+
+def test_serving_workload_alone_equals_the_poisson_mix():
+    """The serving workload's own requests (n log-uniform in [50, 3000], p in
+    3..20, clustered instances seeded 5000 + r, population 512 = 8 x 64, 200
+    generations): 16 of them each run alone, then the same 16 inside a mix of
+    64 with Poisson arrivals (submitted between steps in arrival order) and up
+    to 64 running at once.  Hubs, allocation and both costs are bit-identical,
+    and every fp64 cost is the oracle's pair-form objective."""
+    import multiprocessing as mp
+    import os
+    from concurrent.futures import ProcessPoolExecutor
+
+    total, checked, gens, R, P = 64, 16, 200, 8, 64
+    with ProcessPoolExecutor(min(16, os.cpu_count() or 1), mp_context=mp.get_context("spawn")) as ex:
+        reqs = list(ex.map(synth.serving_request, range(total)))
+    assert max(r.n for r in reqs[:checked]) > 1000
+    alone = []
+    for r in range(checked):
+        inst = reqs[r]
+        with Server(32 * GB, max_active=64, path=PATH_SPLIT_BF16) as s:
+            t = s.submit(inst.W, inst.C, inst.p, islands=R, island_size=P, generations=gens, seed=5000 + r)
+            alone.append(_drain(s, [t])[t])
+    # arrivals: 64 requests over about 40 ticks
+    arrival_tick = np.floor(np.cumsum(np.random.default_rng(77).exponential(40.0 / total, total))).astype(int)
+    mixed, tickets, nxt, peak = {}, {}, 0, 0
+    with Server(32 * GB, max_active=64, path=PATH_SPLIT_BF16) as s:
+        for tick in range(100000):
+            while nxt < total and arrival_tick[nxt] <= tick:
+                inst = reqs[nxt]
+                tickets[s.submit(inst.W, inst.C, inst.p, islands=R, island_size=P, generations=gens,
+                                 seed=5000 + nxt)] = nxt
+                nxt += 1
+            active, _ = s.step()
+            peak = max(peak, active)
+            for t in [t for t in tickets if tickets[t] not in mixed]:
+                res = s.poll(t)
+                if res is not None:
+                    mixed[tickets[t]] = res
+            if len(mixed) == total:
+                break
+    assert len(mixed) == total and peak > 8
+    for r in range(checked):
+        inst, a, m = reqs[r], alone[r], mixed[r]
+        np.testing.assert_array_equal(a["hubs"], m["hubs"])
+        np.testing.assert_array_equal(a["S"], m["S"])
+        assert a["cost_fp32"] == m["cost_fp32"] and a["cost_fp64"] == m["cost_fp64"]
+        assert m["evals"] == 1 + gens * R * P
+        cost.check_allocation(inst.n, m["hubs"], m["S"])
+        ref = cost.pair_cost(inst.W, inst.C, inst.chi, inst.alpha, inst.delta, m["S"])
+        assert m["cost_fp64"] == pytest.approx(ref, rel=1e-12)

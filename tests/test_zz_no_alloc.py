@@ -4,9 +4,10 @@ usaphmp_rescore_fp64_noalloc serves callers that cannot call cudaMalloc (a
 fixed device-memory budget or pool owned by the host application, or a loop
 that cannot take cudaMalloc's implicit synchronisation): it takes only caller
 buffers and keeps its partial sums in a fixed scratch array inside the
-library.  Its costs must match usaphmp_rescore_fp64_dev, the handle-based
-entry point, on consecutive calls (the second call reuses the scratch the
-first one left behind).
+library.  Its costs must match the oracle's fp64 pair-form objective and
+usaphmp_rescore_fp64_dev, the handle-based entry point, on consecutive calls
+(the second call reuses the scratch the first one left behind), for a
+symmetric and an asymmetric C.
 """
 import numpy as np
 import pytest
@@ -29,11 +30,25 @@ def _canonical(inst, hubs, S, stride):
     return hs, slot
 
 
-def test_noalloc_rescore_matches_handle_entry_point_on_two_calls():
+def _asymmetric(inst, seed):
+    """The same instance with C made asymmetric (each arc's cost scaled by its
+    own factor in [0.8, 1.25], diagonal kept at 0)."""
+    rng = np.random.default_rng(seed)
+    C = (inst.C * rng.uniform(0.8, 1.25, inst.C.shape)).astype(np.float32)
+    np.fill_diagonal(C, 0.0)
+    assert not np.array_equal(C, C.T)
+    return synth.Instance(inst.name + "-asym", inst.n, inst.p, inst.W, C)
+
+
+@pytest.mark.parametrize("sym", [True, False], ids=["symmetric_C", "asymmetric_C"])
+def test_noalloc_rescore_matches_the_oracle_and_the_handle_entry_point_on_two_calls(sym):
     need_gpu()
     inst = synth.urand200(seed=91, n=333, p=9)
+    if not sym:
+        inst = _asymmetric(inst, 94)
     W_d, C_d = dev(inst.W), dev(inst.C)
     with Instance.from_instance(inst) as gi:
+        assert gi.info()["c_symmetric"] == int(sym)
         for call, B in enumerate((12, 37)):
             hubs, S = synth.random_population(92 + call, inst.n, inst.p, B)
             hs, slot_pad = _canonical(inst, hubs, S, gi.ns)
@@ -44,7 +59,11 @@ def test_noalloc_rescore_matches_handle_entry_point_on_two_calls():
             gi.rescore_fp64_dev(B, d_hs.data_ptr(), d_pad.data_ptr(), ref.data_ptr(), stream())
             rescore_fp64_noalloc(inst.n, inst.p, B, W_d.data_ptr(), C_d.data_ptr(), inst.chi, inst.alpha,
                                  inst.delta, d_hs.data_ptr(), d_dense.data_ptr(), got.data_ptr(), stream())
-            np.testing.assert_allclose(host(got), host(ref), rtol=RTOL)
+            got_h = host(got)
+            np.testing.assert_allclose(got_h, host(ref), rtol=RTOL)
+            oracle = np.array([ocost.pair_cost(inst.W, inst.C, inst.chi, inst.alpha, inst.delta, S[b])
+                               for b in range(B)])
+            np.testing.assert_allclose(got_h, oracle, rtol=RTOL)
 
 
 def test_noalloc_rescore_rejects_sizes_beyond_its_scratch():
