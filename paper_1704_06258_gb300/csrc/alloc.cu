@@ -8,8 +8,12 @@
 // hub-path routing (eq. 4) the table holds instead the cheapest path cost
 // over arcs between the chromosome's open hubs, zero on the diagonal
 // (Floyd-Warshall in place, one pass per intermediate hub).
-// One block per chromosome; C[i, hub] is read as CT[hub][i], so the p loads
-// of each node are coalesced across the block.
+// C[i, hub] is read as CT[hub][i], so the loads of consecutive nodes are
+// coalesced.  With direct hub arcs (the GA's hot path) one warp allocates one
+// chromosome (k_alloc_warp): no block barriers, and a whole population's
+// warps are resident at once, so the latency of the L2 gathers of one
+// chromosome overlaps that of every other.  Hub-path routing keeps one block
+// per chromosome (k_alloc), whose threads share the Floyd-Warshall passes.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -238,11 +242,200 @@ __global__ void __launch_bounds__(kAllocThreads) k_alloc(const __grid_constant__
   }
 }
 
+// Direct hub arcs: G warps per chromosome (G = 1, 2 or 4 by n alone), four
+// chromosomes' worth of warps per block.  Thread u of a chromosome's 32G
+// takes the four-node groups u, u + 32G, ...: one 16-byte load of
+// CT[hub][i..i+3] per hub, the compares in ascending hub order (lowest hub on
+// ties); hubs serve themselves (the hubs are ascending, so a per-thread
+// pointer finds the hubs inside each group).  The access terms are summed
+// per thread in group order, over each warp by a fixed butterfly and over the
+// G warps in order; the given-slot variant sums in the same order, so both
+// give the same t12 for the same slots, and since G depends on n only a
+// chromosome's t12 does not depend on the batch it is in.
+#ifndef USAPHMP_ALLOC_WARPS
+#define USAPHMP_ALLOC_WARPS 4
+#endif
+constexpr int kAllocWarps = USAPHMP_ALLOC_WARPS;   // warps per block
+
+__host__ __device__ inline int alloc_warps_per_chrom(int n) { return n <= 2048 ? 1 : (n <= 4096 ? 2 : 4); }
+
+// Block offsets of a launch count blocks: task t owns blocks [o[t], o[t+1]),
+// ceil(B_t / (kAllocWarps / G_t)) of them.
+template <bool kNearest>
+__global__ void __launch_bounds__(32 * kAllocWarps) k_alloc_warp(const __grid_constant__ TaskParam tp, int with_chub) {
+  __shared__ int hs_all[kAllocWarps][kMaxP];
+  __shared__ float red[kAllocWarps];
+  pdl_wait();
+  pdl_allow_next();
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int t = task_of(tp.bo, blockIdx.x);
+  const Task& T = task_at(tp, t);
+  const int n = T.in.n, p = T.in.p, ldw = T.in.ldw, ns = T.in.ns;
+  const int G = alloc_warps_per_chrom(n);          // block-uniform
+  const int cpb = kAllocWarps / G;                 // chromosomes per block
+  const int wl = wib % G;                          // warp within its chromosome
+  const int b = (blockIdx.x - tp.bo.o[t]) * cpb + wib / G;
+  const bool live = b < T.pop.B;
+  const float* __restrict__ C = T.in.C;
+  const float* __restrict__ CT = T.in.CT;
+  const float* __restrict__ O = T.in.O;
+  const float* __restrict__ D = T.in.D;
+  const float chi = T.in.chi, delta = T.in.delta;
+  const bool sym = T.in.symmetric != 0;
+  int* hs = hs_all[wib - wl];                      // the chromosome's first warp's row
+  const int u0 = wl * 32 + lane, stride = 32 * G;  // thread within the chromosome
+  bool bad = false;
+  float acc = 0.f;
+  if (live) {
+    uint8_t* __restrict__ slot = T.pop.slot + (long long)b * ns;
+    const uint8_t* __restrict__ slot_in = T.pop.slot_in ? T.pop.slot_in + (long long)b * ns : slot;
+    for (int k = u0; k < p; k += stride) {
+      int v = T.pop.hubs_in ? T.pop.hubs_in[(long long)b * p + k] : T.pop.hubs[(long long)b * p + k];
+      if (v < 0 || v >= n) { bad = true; v = 0; }
+      hs[k] = v;
+      if (T.pop.hubs_in) T.pop.hubs[(long long)b * p + k] = v;
+    }
+  }
+  if (G == 1) __syncwarp(); else __syncthreads();
+  if (live) {
+    uint8_t* __restrict__ slot = T.pop.slot + (long long)b * ns;
+    const uint8_t* __restrict__ slot_in = T.pop.slot_in ? T.pop.slot_in + (long long)b * ns : slot;
+    const int n4 = (n + 3) >> 2;
+    if (kNearest) {
+      int kp = 0;   // first hub not below the current group's first node
+      for (int g = u0; g < n4; g += stride) {
+        const int i0 = g << 2;
+        float4 best = __ldg(reinterpret_cast<const float4*>(CT + (long long)hs[0] * ldw) + g);
+        int s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+        int l = 1;
+        for (; l + 4 <= p; l += 4) {
+          float4 v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) v[u] = __ldg(reinterpret_cast<const float4*>(CT + (long long)hs[l + u] * ldw) + g);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (v[u].x < best.x) { best.x = v[u].x; s0 = l + u; }
+            if (v[u].y < best.y) { best.y = v[u].y; s1 = l + u; }
+            if (v[u].z < best.z) { best.z = v[u].z; s2 = l + u; }
+            if (v[u].w < best.w) { best.w = v[u].w; s3 = l + u; }
+          }
+        }
+        for (; l < p; ++l) {
+          const float4 v = __ldg(reinterpret_cast<const float4*>(CT + (long long)hs[l] * ldw) + g);
+          if (v.x < best.x) { best.x = v.x; s0 = l; }
+          if (v.y < best.y) { best.y = v.y; s1 = l; }
+          if (v.z < best.z) { best.z = v.z; s2 = l; }
+          if (v.w < best.w) { best.w = v.w; s3 = l; }
+        }
+        // hubs inside the group serve themselves
+        while (kp < p && hs[kp] < i0) ++kp;
+        for (int k = kp; k < p && hs[k] < i0 + 4; ++k) {
+          const int h = hs[k];
+          const float own = CT[(long long)h * ldw + h];
+          switch (h - i0) {
+            case 0: s0 = k; best.x = own; break;
+            case 1: s1 = k; best.y = own; break;
+            case 2: s2 = k; best.z = own; break;
+            default: s3 = k; best.w = own; break;
+          }
+        }
+        const float4 o4 = __ldg(reinterpret_cast<const float4*>(O) + g);
+        const float4 d4 = __ldg(reinterpret_cast<const float4*>(D) + g);
+        // one node of the group: access terms (in node order) and slot code
+        auto node = [&](int k, int sk, float cih, float oi, float di) -> uint32_t {
+          const int i = i0 + k;
+          if (i >= n) return (uint32_t)kSlotPad << (8 * k);
+          const float chi_i = sym ? cih : C[(long long)hs[sk] * ldw + i];   // C[h(i), i]
+          acc += access_term(chi, oi, cih, delta, di, chi_i);
+          return (uint32_t)sk << (8 * k);
+        };
+        uint32_t packed = node(0, s0, best.x, o4.x, d4.x);
+        packed |= node(1, s1, best.y, o4.y, d4.y);
+        packed |= node(2, s2, best.z, o4.z, d4.z);
+        packed |= node(3, s3, best.w, o4.w, d4.w);
+        *reinterpret_cast<uint32_t*>(slot + i0) = packed;
+      }
+    } else {
+      for (int g = u0; g < n4; g += stride) {
+        const int i0 = g << 2;
+        const uint32_t codes = *reinterpret_cast<const uint32_t*>(slot_in + i0);
+        int bl[4];
+        float cih[4], chi_i[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          bl[k] = (int)((codes >> (8 * k)) & 0xFFu);
+          if (i0 + k < n && bl[k] >= p) bad = true;
+          if (i0 + k >= n || bl[k] >= p) bl[k] = 0;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int i = min(i0 + k, n - 1);
+          cih[k] = CT[(long long)hs[bl[k]] * ldw + i];                       // C[i, h(i)]
+          chi_i[k] = sym ? cih[k] : C[(long long)hs[bl[k]] * ldw + i];      // C[h(i), i]
+        }
+        const float4 o4 = __ldg(reinterpret_cast<const float4*>(O) + g);
+        const float4 d4 = __ldg(reinterpret_cast<const float4*>(D) + g);
+        const float ok[4] = {o4.x, o4.y, o4.z, o4.w}, dk[4] = {d4.x, d4.y, d4.z, d4.w};
+        uint32_t packed = 0u;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int i = i0 + k;
+          if (i < n) {
+            acc += access_term(chi, ok[k], cih[k], delta, dk[k], chi_i[k]);
+            packed |= (uint32_t)bl[k] << (8 * k);
+          } else {
+            packed |= (uint32_t)kSlotPad << (8 * k);
+          }
+        }
+        *reinterpret_cast<uint32_t*>(slot + i0) = packed;
+      }
+    }
+    for (int i = (n4 << 2) + u0; i < ns; i += stride) slot[i] = kSlotPad;
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(T.pop.status, kStatusBadChromosome);
+  }
+  acc = warp_sum(acc);
+  if (G > 1) {
+    if (lane == 0) red[wib] = acc;
+    __syncthreads();
+    if (wl == 0) {
+      acc = red[wib];
+      for (int w = 1; w < G; ++w) acc += red[wib + w];
+    }
+  }
+  if (live && wl == 0 && lane == 0) T.pop.t12[b] = acc;
+  if (live && (with_chub || plain_global_table(p, ns))) {
+    const int hst = chub_hstride(p), cst = chub_cstride(p);
+    float* ch = T.pop.chub + (long long)b * cst;
+    for (int e = u0; e < cst; e += stride) {
+      const int k = e / hst, l = e - k * hst;
+      ch[e] = (k < p && l < p) ? C[(long long)hs[k] * ldw + hs[l]] : 0.f;
+    }
+  }
+}
+
 void launch_alloc(const TaskSet& ts, bool nearest, bool with_chub, cudaStream_t s) {
   TaskParam tp = make_param(ts);
   for (int t = 0; t < ts.count; ++t) tp.bo.o[t + 1] = tp.bo.o[t] + ts.h[t].pop.B;
-  const int blocks = tp.bo.o[ts.count];
-  if (blocks == 0) return;
+  const int chrom = tp.bo.o[ts.count];
+  if (chrom == 0) return;
+  bool routed = false;
+  for (int t = 0; t < ts.count; ++t) routed |= ts.h[t].in.routing != 0;
+  if (!routed) {
+    // blocks per task from the task's own n: its warps per chromosome, and so
+    // its summation order, never depend on the other tasks of the launch
+    TaskParam tw = make_param(ts);
+    for (int t = 0; t < ts.count; ++t) {
+      const int cpb = kAllocWarps / alloc_warps_per_chrom(ts.h[t].in.n);
+      tw.bo.o[t + 1] = tw.bo.o[t] + (ts.h[t].pop.B + cpb - 1) / cpb;
+    }
+    const int blocks = tw.bo.o[ts.count];
+    if (nearest)
+      launch_pdl(k_alloc_warp<true>, blocks, 32 * kAllocWarps, 0, s, tw, with_chub ? 1 : 0);
+    else
+      launch_pdl(k_alloc_warp<false>, blocks, 32 * kAllocWarps, 0, s, tw, with_chub ? 1 : 0);
+    return;
+  }
+  const int blocks = chrom;
   size_t smem = 0;
   for (int t = 0; t < ts.count; ++t) {
     const int p = ts.h[t].in.p;

@@ -203,12 +203,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_plain(const __grid_constan
   }
 }
 
-int plain_rows(int n, int B) {
-  // Split rows across blocks only when the chromosome groups alone would not
-  // fill the GPU (small populations of large instances).
-  const int groups = (B + 7) / 8;
+int plain_rows(int n, int /*B*/) {
+  // Row splits (blocks per chromosome group, partial sums per chromosome)
+  // grow with n only -- one per 512 rows, a power of two, at most 8 -- so a
+  // chromosome's partial sums, and so its fitness bits, do not depend on the
+  // size of the batch it is evaluated in.
   int rs = 1;
-  while (groups * rs < 2 * 152 && rs * 64 < n) rs <<= 1;
+  while (rs < 8 && rs * 2 * 512 <= n) rs <<= 1;
   return rs;
 }
 

@@ -182,7 +182,7 @@ def test_rescore_fp64_matches_oracle():
 
 
 @pytest.mark.parametrize("path", PATHS, ids=["plain", "split"])
-@pytest.mark.parametrize("B", [511, 512, 2047, 2500])
+@pytest.mark.parametrize("B", [511, 512, 2047, 2500, 4099, 8800])
 def test_host_eval_in_chunks_equals_device_eval(path, B):
     """usaphmp_eval copies and evaluates large populations in chunks; the
     fitness equals the single-launch device call bit for bit."""
