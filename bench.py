@@ -307,6 +307,11 @@ def serving_leg(n_requests, evals_per_s, seed=4242, fixed_rate=50.0):
     fixed = _serve(reqs, fixed_rate, seed, gens, R, P)
     fixed["workload"] = f"the same requests, Poisson arrivals at a fixed {fixed_rate:g} per second"
     out["fixed_rate"] = fixed
+    # the spread the requests' sizes give by themselves: the first 64 at a rate
+    # low enough that they rarely overlap (latency ~ each one's own run time)
+    sparse = _serve(reqs[:64], 8.0, seed, gens, R, P)
+    sparse["workload"] = "the first 64 requests, Poisson arrivals at 8 per second (little overlap)"
+    out["sparse"] = sparse
     return out
 
 
@@ -336,11 +341,18 @@ def _serve(reqs, rate, seed, gens, R, P):
             if not active and not pending and nxt < n_requests:
                 time.sleep(max(0.0, min(0.002, arrivals[nxt] - (time.perf_counter() - t0))))
         makespan = time.perf_counter() - t0
+        st = srv.stats()
     lat = np.array(lat)
     return {"requests": n_requests, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "p99_over_p50": float(np.percentile(lat, 99) / np.percentile(lat, 50)),
             "mean_ms": float(lat.mean()), "evals_per_s": evals / makespan, "makespan_s": makespan,
             "arrival_rate_per_s": rate, "population": R * P, "generations": gens, "max_active": 64,
-            "path": "split-bf16"}
+            "path": "split-bf16",
+            "ticks": st["ticks"], "tick_ms_mean": st["tick_ms_total"] / max(1, st["ticks"]),
+            "tick_ms_max": st["tick_ms_max"],
+            "admission_wait_ms_mean": st["admit_wait_ms_total"] / max(1, st["admitted"]),
+            "admission_wait_ms_max": st["admit_wait_ms_max"],
+            "instance_setup_ms_mean": st["admit_ms_total"] / max(1, st["admitted"])}
 
 
 def rel_error_sample(gi, inst, count=64, seed=99):

@@ -288,15 +288,21 @@ int usaphmp_ga_run_profiled(usaphmp_t h, int32_t generations, void* stream, doub
 /* ---------------------------------------------------------------------------
  * Serving: continuous batching of GA solve requests of differing n and p on
  * one GPU.  Requests queue in FIFO order and are admitted while at most
- * `max_active` (<= 64) run and the device bytes of the running ones
+ * `max_active` (<= 64) are admitted or running and the device bytes of those
  * (usaphmp_server_footprint) stay within `hbm_budget_bytes`; a request that
  * alone exceeds the budget finishes with USAPHMP_EBUSY.  Each
- * usaphmp_server_step admits what fits, then runs up to 8 generations (§5)
- * of every running request -- as many as every one of them still needs, at
- * most 8 -- with one launch per kernel and generation over all of them, then
- * rescores (fp64) and releases the requests that have run all their
- * generations.  A request's result does not depend on which other requests
- * ran beside it.  The server is not thread-safe.
+ * usaphmp_server_step admits what fits, then enqueues up to 8 generations
+ * (§5) of every running request -- as many as every one of them still needs,
+ * at most 8 -- with one launch per kernel and generation over all of them.
+ * A request's result does not depend on which other requests ran beside it.
+ * The step does no device-memory management and waits for no request: a
+ * worker thread of the server makes each admitted request's instance
+ * (stream-ordered allocations from the server's memory pool, which keeps up
+ * to the budget for reuse; the set-up and the initial solution run on the
+ * request's own stream) and finishes each request whose last generation has
+ * been enqueued (fp64 rescoring, copy-out, release), so the step returns
+ * after enqueueing, waiting only when the device is two steps behind.  The
+ * server's calls must come from one thread (the worker is internal).
  * ------------------------------------------------------------------------- */
 typedef struct usaphmp_server_s* usaphmp_server_t;
 
@@ -307,19 +313,35 @@ int usaphmp_server_submit(usaphmp_server_t s, int32_t n, int32_t p, const float*
                           double alpha, double delta, int32_t islands, int32_t island_size, int32_t generations,
                           uint64_t seed, int64_t* ticket);
 
-/* One tick (see above); reports how many requests run and wait. */
+/* One tick (see above); n_active = requests admitted (being made) or
+ * running, n_pending = requests queued for admission plus requests being
+ * finished; either may be NULL. */
 int usaphmp_server_step(usaphmp_server_t s, int32_t* n_active, int32_t* n_pending);
 
+/* Counters since the server was made: ticks and their host wall time (total
+ * and largest, ms), requests admitted into the running set, their wait from
+ * submission to joining it (total and largest, ms), and the worker's time
+ * making their instances (total, ms). */
+typedef struct {
+  int64_t ticks;
+  double tick_ms_total, tick_ms_max;
+  int64_t admitted;
+  double admit_wait_ms_total, admit_wait_ms_max;
+  double admit_ms_total;
+} usaphmp_server_counters;
+int usaphmp_server_stats(usaphmp_server_t s, usaphmp_server_counters* out);
+
 /* 1: finished, *out filled (hubs/S into caller buffers of p and n entries;
- * ms = submit-to-finish wall time) and the ticket forgotten; 0: not finished;
- * < 0: the request failed (message in usaphmp_last_error). */
+ * ms = wall time from submission to the result being ready) and the ticket
+ * forgotten; 0: not finished; < 0: the request failed (message in
+ * usaphmp_last_error). */
 int usaphmp_server_poll(usaphmp_server_t s, int64_t ticket, usaphmp_result* out);
 
 /* Cancels a request between steps: a queued one leaves the queue, a running
- * one stops (its slot and device memory are freed at once).  Its poll then
- * returns USAPHMP_ECANCELED.  USAPHMP_EINVAL for a ticket that is not queued
- * or running (unknown, finished or already cancelled).  Synchronises the
- * server's stream when the request is running. */
+ * or admitted one stops (its slot is free at once; its device memory returns
+ * to the pool once the generations already enqueued for it have run).  Its
+ * poll then returns USAPHMP_ECANCELED.  USAPHMP_EINVAL for a ticket that is
+ * not queued, admitted or running (unknown, finished or already cancelled). */
 int usaphmp_server_cancel(usaphmp_server_t s, int64_t ticket);
 
 /* Device bytes a request of this shape holds while it runs. */

@@ -54,6 +54,11 @@ class Info(ctypes.Structure):
                 ("tc_folded", c_i32)]
 
 
+class ServerStats(ctypes.Structure):
+    _fields_ = [("ticks", c_i64), ("tick_ms_total", c_f64), ("tick_ms_max", c_f64), ("admitted", c_i64),
+                ("admit_wait_ms_total", c_f64), ("admit_wait_ms_max", c_f64), ("admit_ms_total", c_f64)]
+
+
 class UsaphmpError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{ERRORS.get(code, code)}: {msg}")
@@ -92,6 +97,7 @@ _SIGS = {
     "usaphmp_server_footprint": (c_i32, [c_i32, c_i32, c_i32, c_i32, ctypes.POINTER(c_i64)]),
     "usaphmp_server_destroy": (None, [c_vp]),
     "usaphmp_server_cancel": (c_i32, [c_vp, c_i64]),
+    "usaphmp_server_stats": (c_i32, [c_vp, ctypes.POINTER(ServerStats)]),
     "usaphmp_debug_fail_allocations": (c_i32, [c_i32]),
     "usaphmp_selftest_wait_timeout": (c_i32, [c_i64, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(c_i64)]),
     "usaphmp_ga_islands": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
@@ -414,6 +420,12 @@ class Server:
         check(0 if rc == 1 else rc)
         return {"hubs": hubs, "S": S, "cost_fp64": r.cost_fp64, "cost_fp32": r.cost_fp32, "evals": r.evals,
                 "ms": r.ms}
+
+    def stats(self):
+        """usaphmp_server_stats as a dict."""
+        st = ServerStats()
+        check(lib().usaphmp_server_stats(self.h, ctypes.byref(st)))
+        return {name: getattr(st, name) for name, _ in ServerStats._fields_}
 
     @staticmethod
     def footprint(n, p, islands, island_size):

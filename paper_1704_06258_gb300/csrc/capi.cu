@@ -50,19 +50,35 @@ int cuda_fail(cudaError_t e, const char* what) {
 // before one fails; negative = never.
 std::atomic<int> g_fail_after{-1};
 
+// Device allocations of a handle: cudaMalloc / cudaFree, or, for a handle
+// created with a memory pool (the serving loop's), stream-ordered
+// allocations from that pool on the handle's stream, which neither
+// allocate from nor return memory to the device nor synchronise it.
+struct AllocCtx {
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t stream = nullptr;
+};
+
 template <class T>
-cudaError_t dalloc(T** p, size_t count) {
+cudaError_t dalloc(const AllocCtx& a, T** p, size_t count) {
   int left = g_fail_after.load();
   while (left >= 0) {
     if (left == 0) return cudaErrorMemoryAllocation;
     if (g_fail_after.compare_exchange_weak(left, left - 1)) break;
   }
-  return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * std::max<size_t>(count, 1));
+  const size_t bytes = sizeof(T) * std::max<size_t>(count, 1);
+  if (a.pool) return cudaMallocFromPoolAsync(reinterpret_cast<void**>(p), bytes, a.pool, a.stream);
+  return cudaMalloc(reinterpret_cast<void**>(p), bytes);
 }
 
 template <class T>
-void dfree(T*& p) {
-  if (p) cudaFree(p);
+void dfree(const AllocCtx& a, T*& p) {
+  if (p) {
+    if (a.pool)
+      cudaFreeAsync(p, a.stream);
+    else
+      cudaFree(p);
+  }
   p = nullptr;
 }
 
@@ -77,8 +93,8 @@ struct Pop {
   float* chub = nullptr;
   float* part = nullptr;
   float* fit = nullptr;
-  void release() {
-    dfree(mask); dfree(hubs); dfree(slot); dfree(t12); dfree(chub); dfree(part); dfree(fit);
+  void release(const AllocCtx& a) {
+    dfree(a, mask); dfree(a, hubs); dfree(a, slot); dfree(a, t12); dfree(a, chub); dfree(a, part); dfree(a, fit);
     cap = 0;
     part_cap = 0;
   }
@@ -87,6 +103,7 @@ struct Pop {
 }  // namespace
 
 struct usaphmp_s {
+  AllocCtx ac;  // how this handle allocates device memory (pool and stream, or cudaMalloc)
   int n = 0, p = 0, ldw = 0, ns = 0, nw = 0;
   double chi = 0, alpha = 0, delta = 0;
   int symmetric = 0;
@@ -98,15 +115,15 @@ struct usaphmp_s {
   float* D = nullptr;
   __nv_bfloat16* Whi = nullptr;
   __nv_bfloat16* Wlo = nullptr;
-  void* tmaps = nullptr;  // two CUtensorMap in device memory
+  char* tmaps = nullptr;  // two CUtensorMap in device memory
   usaphmp_params prm{};
   TcTile tile{};  // tile shape of the tensor-core evaluator (usaphmp_set_tile / usaphmp_autotune)
   int num_sms = 0;
   cudaStream_t stream = nullptr;
   uint32_t* d_status = nullptr;
   int* d_bad = nullptr;
-  uint32_t* h_status = nullptr;  // pinned
-  int* h_bad = nullptr;          // pinned
+  uint32_t* h_status = nullptr;  // pinned (pageable for a pool handle: no host-allocation synchronisation)
+  int* h_bad = nullptr;
   double* d_dscratch = nullptr;
   double* d_cost = nullptr;
   double* d_rpart = nullptr;
@@ -179,11 +196,11 @@ int ensure_fp64(usaphmp_s* h, int B) {
   if (!use_fp64(h)) return USAPHMP_OK;
   const bool paths = h->prm.routing != USAPHMP_ROUTE_DIRECT;
   if (h->cap64 >= B && (!paths || h->d_paths64)) return USAPHMP_OK;
-  dfree(h->d_part64); dfree(h->d_cost64); dfree(h->d_paths64);
+  dfree(h->ac, h->d_part64); dfree(h->ac, h->d_cost64); dfree(h->ac, h->d_paths64);
   h->cap64 = 0;
-  CK(dalloc(&h->d_part64, (size_t)B * rescore_parts(h->n)));
-  CK(dalloc(&h->d_cost64, (size_t)B));
-  if (paths) CK(dalloc(&h->d_paths64, (size_t)B * h->p * h->p));
+  CK(dalloc(h->ac, &h->d_part64, (size_t)B * rescore_parts(h->n)));
+  CK(dalloc(h->ac, &h->d_cost64, (size_t)B));
+  if (paths) CK(dalloc(h->ac, &h->d_paths64, (size_t)B * h->p * h->p));
   h->cap64 = B;
   return USAPHMP_OK;
 }
@@ -192,14 +209,14 @@ int ensure_fp64(usaphmp_s* h, int B) {
 // flow sums), made on first use.
 int ensure_ls(usaphmp_s* h, cudaStream_t s) {
   if (h->d_WT && h->d_OD64) return USAPHMP_OK;
-  dfree(h->d_WT); dfree(h->d_OD64);
+  dfree(h->ac, h->d_WT); dfree(h->ac, h->d_OD64);
   float* wt = nullptr;
   double* od = nullptr;
-  CK(dalloc(&wt, (size_t)h->n * h->ldw));
-  const cudaError_t e = dalloc(&od, (size_t)2 * h->n);
+  CK(dalloc(h->ac, &wt, (size_t)h->n * h->ldw));
+  const cudaError_t e = dalloc(h->ac, &od, (size_t)2 * h->n);
   if (e != cudaSuccess) {
-    dfree(wt);
-    return cuda_fail(e, "dalloc(&od, 2 * n)");
+    dfree(h->ac, wt);
+    return cuda_fail(e, "dalloc(h->ac, &od, 2 * n)");
   }
   CK(cudaMemsetAsync(wt, 0, sizeof(float) * (size_t)h->n * h->ldw, s));
   launch_ls_prepare(h->W, h->n, h->ldw, wt, od, s);
@@ -229,14 +246,14 @@ size_t part_elems(const usaphmp_s* h, int B) {
 int ensure_pop(usaphmp_s* h, Pop& P, int B, size_t need_part = 0) {
   need_part = std::max(need_part, part_elems(h, B));
   if (P.cap >= B && P.part_cap >= need_part) return USAPHMP_OK;
-  P.release();
-  CK(dalloc(&P.mask, (size_t)B * h->nw));
-  CK(dalloc(&P.hubs, (size_t)B * h->p));
-  CK(dalloc(&P.slot, (size_t)B * h->ns));
-  CK(dalloc(&P.t12, (size_t)B));
-  CK(dalloc(&P.chub, (size_t)B * chub_cstride(h->p)));
-  CK(dalloc(&P.part, need_part));
-  CK(dalloc(&P.fit, (size_t)B));
+  P.release(h->ac);
+  CK(dalloc(h->ac, &P.mask, (size_t)B * h->nw));
+  CK(dalloc(h->ac, &P.hubs, (size_t)B * h->p));
+  CK(dalloc(h->ac, &P.slot, (size_t)B * h->ns));
+  CK(dalloc(h->ac, &P.t12, (size_t)B));
+  CK(dalloc(h->ac, &P.chub, (size_t)B * chub_cstride(h->p)));
+  CK(dalloc(h->ac, &P.part, need_part));
+  CK(dalloc(h->ac, &P.fit, (size_t)B));
   P.cap = B;
   P.part_cap = need_part;
   return USAPHMP_OK;
@@ -336,14 +353,18 @@ int encode_tmaps(usaphmp_s* h) {
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(USAPHMP_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
   }
-  CK(cudaMalloc(&h->tmaps, sizeof(maps)));
-  CK(cudaMemcpy(h->tmaps, maps, sizeof(maps), cudaMemcpyHostToDevice));
+  CK(dalloc(h->ac, &h->tmaps, sizeof(maps)));
+  if (h->ac.pool)
+    CK(cudaMemcpyAsync(h->tmaps, maps, sizeof(maps), cudaMemcpyHostToDevice, h->ac.stream));   // pageable: staged now
+  else
+    CK(cudaMemcpy(h->tmaps, maps, sizeof(maps), cudaMemcpyHostToDevice));
   return USAPHMP_OK;
 }
 
 int create_common(usaphmp_s* h, const float* W, const float* C, bool dev, cudaStream_t s) {
   const int n = h->n;
   CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+  h->ac.stream = h->stream;
   int dev_id = 0;
   CK(cudaGetDevice(&dev_id));
   CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev_id));
@@ -353,18 +374,23 @@ int create_common(usaphmp_s* h, const float* W, const float* C, bool dev, cudaSt
   prepare_eval_tc();
   CK(cudaGetLastError());
   const size_t mat = (size_t)n * h->ldw;
-  CK(dalloc(&h->W, mat));
-  CK(dalloc(&h->C, mat));
-  CK(dalloc(&h->O, h->ns));   // padded to ns: the allocation kernel reads four nodes at a time
-  CK(dalloc(&h->D, h->ns));
-  CK(dalloc(&h->Whi, mat));
-  CK(dalloc(&h->Wlo, mat));
-  CK(dalloc(&h->d_status, 1));
-  CK(dalloc(&h->d_bad, 1));
-  CK(dalloc(&h->d_dscratch, n));
-  CK(dalloc(&h->d_total, 1));
-  CK(cudaMallocHost(&h->h_status, sizeof(uint32_t)));
-  CK(cudaMallocHost(&h->h_bad, sizeof(int)));
+  CK(dalloc(h->ac, &h->W, mat));
+  CK(dalloc(h->ac, &h->C, mat));
+  CK(dalloc(h->ac, &h->O, h->ns));   // padded to ns: the allocation kernel reads four nodes at a time
+  CK(dalloc(h->ac, &h->D, h->ns));
+  CK(dalloc(h->ac, &h->Whi, mat));
+  CK(dalloc(h->ac, &h->Wlo, mat));
+  CK(dalloc(h->ac, &h->d_status, 1));
+  CK(dalloc(h->ac, &h->d_bad, 1));
+  CK(dalloc(h->ac, &h->d_dscratch, n));
+  CK(dalloc(h->ac, &h->d_total, 1));
+  if (h->ac.pool) {
+    h->h_status = new uint32_t[1];
+    h->h_bad = new int[1];
+  } else {
+    CK(cudaMallocHost(&h->h_status, sizeof(uint32_t)));
+    CK(cudaMallocHost(&h->h_bad, sizeof(int)));
+  }
   if (!dev) s = h->stream;
   CK(cudaMemsetAsync(h->W, 0, mat * sizeof(float), s));
   CK(cudaMemsetAsync(h->C, 0, mat * sizeof(float), s));
@@ -390,12 +416,12 @@ int create_common(usaphmp_s* h, const float* W, const float* C, bool dev, cudaSt
   // symmetric C: every hub-to-hub table (direct or hub paths) is symmetric,
   // so the tensor-core evaluator takes the folded, upper-triangular U
   if (h->symmetric) {
-    CK(dalloc(&h->Ufold, mat));
+    CK(dalloc(h->ac, &h->Ufold, mat));
     launch_split_bf16_upper(h->W, h->Whi, h->Wlo, h->Ufold, n, h->ldw, s);
   } else
     launch_split_bf16(h->W, h->Whi, h->Wlo, (long long)mat, s);
   if (!h->symmetric) {
-    CK(dalloc(&h->CTbuf, mat));
+    CK(dalloc(h->ac, &h->CTbuf, mat));
     CK(cudaMemsetAsync(h->CTbuf, 0, mat * sizeof(float), s));
     launch_transpose(h->C, h->CTbuf, n, h->ldw, s);
     CK(cudaGetLastError());
@@ -406,7 +432,7 @@ int create_common(usaphmp_s* h, const float* W, const float* C, bool dev, cudaSt
 }
 
 int create_impl(int32_t n, int32_t p, const float* W, const float* C, double chi, double alpha, double delta,
-                bool dev, void* stream, usaphmp_t* out) {
+                bool dev, void* stream, usaphmp_t* out, cudaMemPool_t pool = nullptr) {
   const NvtxRange nvtx_range("usaphmp_create");
   if (!out) return fail(USAPHMP_EINVAL, "out is NULL");
   *out = nullptr;
@@ -416,6 +442,7 @@ int create_impl(int32_t n, int32_t p, const float* W, const float* C, double chi
   if (!(chi >= 0) || !(alpha >= 0) || !(delta >= 0) || chi > 1e30 || alpha > 1e30 || delta > 1e30)
     return fail(USAPHMP_EINVAL, "chi, alpha, delta must be finite and >= 0");
   usaphmp_s* h = new usaphmp_s();
+  h->ac.pool = dev ? nullptr : pool;   // pool handles are made from host arrays on their own stream
   h->n = n; h->p = p;
   h->ldw = round_up(n, 8);
   h->ns = round_up(n, 64);
@@ -488,29 +515,29 @@ int ensure_ga(usaphmp_s* h) {
   RET(ensure_pop(h, h->one, 1));
   if (h->ga_R != R || h->ga_P != P || !h->anc) {
     h->ga_R = h->ga_P = 0;  // stays 0 unless every buffer below is allocated
-    dfree(h->anc); dfree(h->anc_fit); dfree(h->best); dfree(h->best_fit); dfree(h->gen); dfree(h->mask0);
-    dfree(h->done);
-    CK(dalloc(&h->done, 1));
-    CK(cudaMemset(h->done, 0, sizeof(int)));
-    CK(dalloc(&h->anc, (size_t)R * h->nw));
-    CK(dalloc(&h->anc_fit, (size_t)R));
-    CK(dalloc(&h->best, (size_t)h->nw));
-    CK(dalloc(&h->best_fit, 1));
-    CK(dalloc(&h->gen, 1));
-    CK(dalloc(&h->mask0, (size_t)h->nw));
+    dfree(h->ac, h->anc); dfree(h->ac, h->anc_fit); dfree(h->ac, h->best); dfree(h->ac, h->best_fit); dfree(h->ac, h->gen); dfree(h->ac, h->mask0);
+    dfree(h->ac, h->done);
+    CK(dalloc(h->ac, &h->done, 1));
+    CK(h->ac.pool ? cudaMemsetAsync(h->done, 0, sizeof(int), h->ac.stream) : cudaMemset(h->done, 0, sizeof(int)));
+    CK(dalloc(h->ac, &h->anc, (size_t)R * h->nw));
+    CK(dalloc(h->ac, &h->anc_fit, (size_t)R));
+    CK(dalloc(h->ac, &h->best, (size_t)h->nw));
+    CK(dalloc(h->ac, &h->best_fit, 1));
+    CK(dalloc(h->ac, &h->gen, 1));
+    CK(dalloc(h->ac, &h->mask0, (size_t)h->nw));
     h->ga_R = R;
     h->ga_P = P;
   }
   const int np = rescore_parts(h->n);
   if (h->rpart_cap < np) {
-    dfree(h->d_rpart); dfree(h->d_cost);
-    CK(dalloc(&h->d_rpart, (size_t)np * 2));
-    CK(dalloc(&h->d_cost, 2));
+    dfree(h->ac, h->d_rpart); dfree(h->ac, h->d_cost);
+    CK(dalloc(h->ac, &h->d_rpart, (size_t)np * 2));
+    CK(dalloc(h->ac, &h->d_cost, 2));
     h->rpart_cap = np;
   }
-  if (!h->d_dist64) CK(dalloc(&h->d_dist64, (size_t)h->p * h->p));
-  if (!h->d_ls) CK(dalloc(&h->d_ls, local_search_scratch_doubles(h->n, h->p)));
-  if (!h->d_ls_count) CK(dalloc(&h->d_ls_count, 2));
+  if (!h->d_dist64) CK(dalloc(h->ac, &h->d_dist64, (size_t)h->p * h->p));
+  if (!h->d_ls) CK(dalloc(h->ac, &h->d_ls, local_search_scratch_doubles(h->n, h->p)));
+  if (!h->d_ls_count) CK(dalloc(h->ac, &h->d_ls_count, 2));
   RET(ensure_fp64(h, R * P));
   return USAPHMP_OK;
 }
@@ -557,6 +584,13 @@ std::vector<int32_t> mask_to_hubs(const std::vector<uint32_t>& m, int n) {
 
 int usaphmp::report_error(int code, const std::string& msg) { return fail(code, msg); }
 
+int usaphmp::create_pooled(int32_t n, int32_t p, const float* W, const float* C, double chi, double alpha,
+                           double delta, cudaMemPool_t pool, usaphmp_t* out) {
+  return create_impl(n, p, W, C, chi, alpha, delta, false, nullptr, out, pool);
+}
+
+cudaStream_t usaphmp::handle_stream(const usaphmp_s* h) { return h->stream; }
+
 const Task& usaphmp::handle_ga_task(const usaphmp_s* h) { return h->ga_task; }
 bool usaphmp::handle_uses_tc(const usaphmp_s* h) { return use_tc(h); }
 void usaphmp::handle_note_generations(usaphmp_s* h, int g) {
@@ -599,20 +633,25 @@ void usaphmp_destroy(usaphmp_t h) {
   if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   for (int k = 0; k < 6; ++k)
     if (h->prof_ev[k]) cudaEventDestroy(h->prof_ev[k]);
-  dfree(h->W); dfree(h->C); dfree(h->CTbuf); dfree(h->Ufold); dfree(h->O); dfree(h->D); dfree(h->Whi); dfree(h->Wlo);
-  if (h->tmaps) cudaFree(h->tmaps);
-  dfree(h->d_status); dfree(h->d_bad); dfree(h->d_dscratch); dfree(h->d_cost); dfree(h->d_rpart);
-  dfree(h->d_dist64); dfree(h->d_total); dfree(h->d_ls); dfree(h->d_ls_count); dfree(h->d_WT); dfree(h->d_OD64);
-  dfree(h->d_ls_batch);
+  dfree(h->ac, h->W); dfree(h->ac, h->C); dfree(h->ac, h->CTbuf); dfree(h->ac, h->Ufold); dfree(h->ac, h->O); dfree(h->ac, h->D); dfree(h->ac, h->Whi); dfree(h->ac, h->Wlo);
+  dfree(h->ac, h->tmaps);
+  dfree(h->ac, h->d_status); dfree(h->ac, h->d_bad); dfree(h->ac, h->d_dscratch); dfree(h->ac, h->d_cost); dfree(h->ac, h->d_rpart);
+  dfree(h->ac, h->d_dist64); dfree(h->ac, h->d_total); dfree(h->ac, h->d_ls); dfree(h->ac, h->d_ls_count); dfree(h->ac, h->d_WT); dfree(h->ac, h->d_OD64);
+  dfree(h->ac, h->d_ls_batch);
   h->ls_batch_cap = 0;
-  dfree(h->d_part64); dfree(h->d_cost64); dfree(h->d_paths64);
-  if (h->h_status) cudaFreeHost(h->h_status);
-  if (h->h_bad) cudaFreeHost(h->h_bad);
-  h->ev.release(); h->ga.release(); h->one.release();
-  dfree(h->d_hubs_in); dfree(h->d_S_in); dfree(h->d_fit_out);
+  dfree(h->ac, h->d_part64); dfree(h->ac, h->d_cost64); dfree(h->ac, h->d_paths64);
+  if (h->ac.pool) {
+    delete[] h->h_status;
+    delete[] h->h_bad;
+  } else {
+    if (h->h_status) cudaFreeHost(h->h_status);
+    if (h->h_bad) cudaFreeHost(h->h_bad);
+  }
+  h->ev.release(h->ac); h->ga.release(h->ac); h->one.release(h->ac);
+  dfree(h->ac, h->d_hubs_in); dfree(h->ac, h->d_S_in); dfree(h->ac, h->d_fit_out);
   if (h->h_fit_out) cudaFreeHost(h->h_fit_out);
-  dfree(h->anc); dfree(h->anc_fit); dfree(h->best); dfree(h->best_fit); dfree(h->gen); dfree(h->mask0);
-  dfree(h->done);
+  dfree(h->ac, h->anc); dfree(h->ac, h->anc_fit); dfree(h->ac, h->best); dfree(h->ac, h->best_fit); dfree(h->ac, h->gen); dfree(h->ac, h->mask0);
+  dfree(h->ac, h->done);
   if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -784,13 +823,13 @@ int usaphmp_eval(usaphmp_t h, int32_t B, const int32_t* hubs, const int32_t* S, 
   if (!hubs || !S || !fitness) return fail(USAPHMP_EINVAL, "NULL argument");
   cudaStream_t s = h->stream;
   if (h->in_cap < B) {
-    dfree(h->d_hubs_in); dfree(h->d_S_in); dfree(h->d_fit_out);
+    dfree(h->ac, h->d_hubs_in); dfree(h->ac, h->d_S_in); dfree(h->ac, h->d_fit_out);
     if (h->h_fit_out) cudaFreeHost(h->h_fit_out);
     h->h_fit_out = nullptr;
     h->in_cap = 0;
-    CK(dalloc(&h->d_hubs_in, (size_t)B * h->p));
-    CK(dalloc(&h->d_S_in, (size_t)B * h->n));
-    CK(dalloc(&h->d_fit_out, (size_t)B));
+    CK(dalloc(h->ac, &h->d_hubs_in, (size_t)B * h->p));
+    CK(dalloc(h->ac, &h->d_S_in, (size_t)B * h->n));
+    CK(dalloc(h->ac, &h->d_fit_out, (size_t)B));
     CK(cudaMallocHost(&h->h_fit_out, sizeof(float) * B));
     h->in_cap = B;
   }
@@ -959,9 +998,9 @@ int usaphmp_local_search_dev(usaphmp_t h, int32_t B, const int32_t* hubs, uint8_
   const size_t need = (size_t)B * local_search_scratch_doubles(h->n, h->p);
   if (h->ls_batch_cap < need) {
     CK(cudaStreamSynchronize(s));  // a previous call's kernels may still use the old scratch
-    dfree(h->d_ls_batch);
+    dfree(h->ac, h->d_ls_batch);
     h->ls_batch_cap = 0;
-    CK(dalloc(&h->d_ls_batch, need));
+    CK(dalloc(h->ac, &h->d_ls_batch, need));
     h->ls_batch_cap = need;
   }
   launch_local_search(inst_of(h), h->d_WT, h->d_OD64, B, hubs, slot, max_sweeps, h->d_ls_batch, moves, sweeps, s);
@@ -978,19 +1017,19 @@ int usaphmp_rescore_fp64_dev(usaphmp_t h, int32_t B, const int32_t* hubs, const 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   double* part = nullptr;
   double* dist = nullptr;
-  CK(dalloc(&part, (size_t)rescore_parts(h->n) * B));
+  CK(dalloc(h->ac, &part, (size_t)rescore_parts(h->n) * B));
   if (h->prm.routing != USAPHMP_ROUTE_DIRECT) {
-    const cudaError_t ea = dalloc(&dist, (size_t)B * h->p * h->p);
+    const cudaError_t ea = dalloc(h->ac, &dist, (size_t)B * h->p * h->p);
     if (ea != cudaSuccess) {
-      cudaFree(part);
+      dfree(h->ac, part);
       return cuda_fail(ea, "dalloc(hub-path tables)");
     }
   }
   launch_rescore(inst_of(h), B, hubs, slot, part, cost, s, dist, output_scale(h));
   cudaError_t e = cudaGetLastError();
   cudaError_t e2 = cudaStreamSynchronize(s);
-  cudaFree(part);
-  if (dist) cudaFree(dist);
+  dfree(h->ac, part);
+  dfree(h->ac, dist);
   CK(e);
   CK(e2);
   return USAPHMP_OK;

@@ -173,6 +173,12 @@ int report_error(int code, const std::string& msg);
 struct usaphmp_s;
 namespace usaphmp {
 const Task& handle_ga_task(const usaphmp_s* h);
+// A handle whose device memory comes from `pool` by stream-ordered
+// allocations on its own stream (handle_stream), so that making and
+// destroying it never synchronises the device (the serving loop's handles).
+int create_pooled(int32_t n, int32_t p, const float* W, const float* C, double chi, double alpha, double delta,
+                  cudaMemPool_t pool, usaphmp_s** out);
+cudaStream_t handle_stream(const usaphmp_s* h);
 bool handle_uses_tc(const usaphmp_s* h);
 void handle_note_generations(usaphmp_s* h, int generations);
 // Device bytes a handle holds for an instance of n nodes and p hubs running
