@@ -418,12 +418,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < kMaxStages; ++s) {
       ptx::mbar_init(bars.full_tma(s), 1);
-      ptx::mbar_init(bars.full_oh(s), 256);
+      ptx::mbar_init(bars.full_oh(s), 8);                 // one arrival per producer warp
       ptx::mbar_init(bars.empty(s), 1);
     }
     for (int b = 0; b < 2; ++b) {
       ptx::mbar_init(bars.tfull(b), 1);
-      ptx::mbar_init(bars.tempty(b), 32 * kEpiWarps);
+      ptx::mbar_init(bars.tempty(b), kEpiWarps);          // one arrival per epilogue warp
     }
     ptx::mbar_init(bars.drain(), 1);
     ptx::mbar_init(bars.slab_full(), 1);
@@ -575,11 +575,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       } else {
         epi_chromosomes<1>(ea);
       }
-      // every accumulator read of this warp has completed: release the buffer
+      // every accumulator read of this warp has completed (each lane waited
+      // for its loads): release the buffer, one arrival for the warp
       ptx::tc_fence_before();
-      ptx::mbar_arrive(bars.tempty(buf));
       __syncwarp();
-      if (lane == 0) ptx::mbar_arrive(bars.slab_empty());
+      if (lane == 0) {
+        ptx::mbar_arrive(bars.tempty(buf));
+        ptx::mbar_arrive(bars.slab_empty());
+      }
     }
   } else if (warp >= kProdWarp0) {
     // -------------------------------------------------------- one-hot producers
@@ -642,8 +645,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (uint32_t q = 0; q < 8; ++q) st_shared_v4(dst + ((q ^ swz) << 4), zero4);
         }
+        // each lane makes its stores visible to the tensor core, then the warp
+        // arrives once
         ptx::fence_proxy_async_smem();
-        ptx::mbar_arrive(bars.full_oh(s));
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(bars.full_oh(s));
       }
     }
   }
