@@ -207,54 +207,27 @@ __device__ __forceinline__ int tile_of_round(int r, bool snake) {
 // diagonal) the blocks left of column 128 m add nothing.
 __device__ __forceinline__ int k_begin(const Task& T, int m) { return T.in.wtri ? (m * BM) / BK : 0; }
 
-// 0x80 in every byte of x that is zero, 0 elsewhere (no carry crosses a
-// byte: each byte's low 7 bits + 0x7F stays below 0x100).
-__device__ __forceinline__ uint32_t zero_byte_flags(uint32_t x) {
-  return ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) & 0x80808080u;
-}
-
-// prmt with sign replication: result byte k = 0xFF or 0x00, the top bit of
-// the source byte chosen by selector nibble k (bit 3 of the nibble set).
-__device__ __forceinline__ uint32_t prmt_sign(uint32_t x, uint32_t sel) {
+// 8 slot codes (two words) -> 8 bf16 values, 1.0 where the code equals the
+// row's slot l, 0 elsewhere, element k in the k-th 16-bit lane: each code c
+// becomes the bf16 bit pattern 0x4000 | c (a finite normal number, distinct
+// for every byte c; prmt with 0x40 bytes), and one bf16x2 compare against
+// lpair = the same pattern of l in both halves gives 1.0 or 0.0 per half.
+__device__ __forceinline__ uint32_t bf16x2_eq(uint32_t a, uint32_t b) {
   uint32_t r;
-  asm("prmt.b32 %0, %1, 0, %2;" : "=r"(r) : "r"(x), "r"(sel));
+  asm("set.eq.bf16x2.bf16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
   return r;
 }
-
-// The one-hot operand holds kOneHot = 2.0 (bf16 0x4000: a zero low byte) in
-// place of 1.0; every accumulator is then exactly twice M_b = W A_b and the
-// epilogue scales the chromosome's sum back by kOneHotInv (exact in fp32).
-constexpr float kOneHotInv = 0.5f;
-
-// 8 slot codes (two words) -> 8 bf16 values, kOneHot where the code equals l
-// (lrep = l in every byte), 0 elsewhere; element k goes to the k-th 16-bit
-// lane in memory order.  Exact equality test for every code and l.
-__device__ __forceinline__ uint4 onehot8(uint32_t w0, uint32_t w1, uint32_t lrep) {
-  const uint32_t z0 = zero_byte_flags(w0 ^ lrep), z1 = zero_byte_flags(w1 ^ lrep);
-  uint4 o;
-  o.x = prmt_sign(z0, 0x9988u) & 0x40004000u;
-  o.y = prmt_sign(z0, 0xBBAAu) & 0x40004000u;
-  o.z = prmt_sign(z1, 0x9988u) & 0x40004000u;
-  o.w = prmt_sign(z1, 0xBBAAu) & 0x40004000u;
-  return o;
+__device__ __forceinline__ uint32_t codes_to_bf16x2(uint32_t w, uint32_t sel) {
+  uint32_t r;
+  asm("prmt.b32 %0, %1, 0x40404040, %2;" : "=r"(r) : "r"(w), "r"(sel));
+  return r;
 }
-
-// 0x40 in every byte of w that equals l, when every code is below 63 or the
-// pad 0xFF and l <= 62 (p <= 63): the byte y = code ^ l is then in [0, 0x3F]
-// or [0xC1, 0xFF], (y | 0x40) - 1 borrows from no byte and clears bit 6
-// exactly when y == 0.
-__device__ __forceinline__ uint32_t eq_flags40(uint32_t w, uint32_t lrep) {
-  return ~(((w ^ lrep) | 0x40404040u) - 0x01010101u) & 0x40404040u;
-}
-
-// onehot8 for p <= 63: the flag byte is already the high byte of kOneHot.
-__device__ __forceinline__ uint4 onehot8_small(uint32_t w0, uint32_t w1, uint32_t lrep) {
-  const uint32_t f0 = eq_flags40(w0, lrep), f1 = eq_flags40(w1, lrep);
+__device__ __forceinline__ uint4 onehot8_set(uint32_t w0, uint32_t w1, uint32_t lpair) {
   uint4 o;
-  asm("prmt.b32 %0, %1, 0, 0x1404;" : "=r"(o.x) : "r"(f0));
-  asm("prmt.b32 %0, %1, 0, 0x3424;" : "=r"(o.y) : "r"(f0));
-  asm("prmt.b32 %0, %1, 0, 0x1404;" : "=r"(o.z) : "r"(f1));
-  asm("prmt.b32 %0, %1, 0, 0x3424;" : "=r"(o.w) : "r"(f1));
+  o.x = bf16x2_eq(codes_to_bf16x2(w0, 0x5140u), lpair);
+  o.y = bf16x2_eq(codes_to_bf16x2(w0, 0x5342u), lpair);
+  o.z = bf16x2_eq(codes_to_bf16x2(w1, 0x5140u), lpair);
+  o.w = bf16x2_eq(codes_to_bf16x2(w1, 0x5342u), lpair);
   return o;
 }
 
@@ -319,7 +292,7 @@ __device__ __forceinline__ void epi_chromosomes(const EpiArgs& a) {
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (a.lane == 0) a.out[c] = acc * kOneHotInv;
+    if (a.lane == 0) a.out[c] = acc;
   }
 }
 
@@ -364,7 +337,7 @@ __device__ __forceinline__ void epi_finish(const EpiArgs& a, int c, const uint32
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (a.lane == 0) a.out[c] = acc * kOneHotInv;
+  if (a.lane == 0) a.out[c] = acc;
 }
 
 template <int WID, int LM>
@@ -601,9 +574,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int kb0 = k_begin(T, tr.m);
       const bool valid = r < nchrom * p;   // rows in [nchrom*p, nmma) are zero
       const bool write = r < nmma;
-      const bool small = p <= 63;
       const int c = valid ? r / p : 0;
-      const uint32_t lrep = (uint32_t)(valid ? r - c * p : 0) * 0x01010101u;
+      const uint32_t lpair = (0x4000u | (uint32_t)(valid ? r - c * p : 0)) * 0x00010001u;
       const uint8_t* srow = T.pop.slot + (long long)(b0 + c) * ns;
       const uint32_t swz = (uint32_t)(r & 7);
       const uint4* src = reinterpret_cast<const uint4*>(srow);
@@ -623,24 +595,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int s = ring.s;
         if (!(ok = wait_warp(bars.empty(s), ring.ph ^ 1u, abort_flag, status))) break;
         const uint32_t dst = base + s * STAGE_BYTES + 2 * A_BYTES + (uint32_t)r * 128u;
-        if (valid && small) {
-          st_shared_v4(dst + ((0u ^ swz) << 4), onehot8_small(q0.x, q0.y, lrep));
-          st_shared_v4(dst + ((1u ^ swz) << 4), onehot8_small(q0.z, q0.w, lrep));
-          st_shared_v4(dst + ((2u ^ swz) << 4), onehot8_small(q1.x, q1.y, lrep));
-          st_shared_v4(dst + ((3u ^ swz) << 4), onehot8_small(q1.z, q1.w, lrep));
-          st_shared_v4(dst + ((4u ^ swz) << 4), onehot8_small(q2.x, q2.y, lrep));
-          st_shared_v4(dst + ((5u ^ swz) << 4), onehot8_small(q2.z, q2.w, lrep));
-          st_shared_v4(dst + ((6u ^ swz) << 4), onehot8_small(q3.x, q3.y, lrep));
-          st_shared_v4(dst + ((7u ^ swz) << 4), onehot8_small(q3.z, q3.w, lrep));
-        } else if (valid) {
-          st_shared_v4(dst + ((0u ^ swz) << 4), onehot8(q0.x, q0.y, lrep));
-          st_shared_v4(dst + ((1u ^ swz) << 4), onehot8(q0.z, q0.w, lrep));
-          st_shared_v4(dst + ((2u ^ swz) << 4), onehot8(q1.x, q1.y, lrep));
-          st_shared_v4(dst + ((3u ^ swz) << 4), onehot8(q1.z, q1.w, lrep));
-          st_shared_v4(dst + ((4u ^ swz) << 4), onehot8(q2.x, q2.y, lrep));
-          st_shared_v4(dst + ((5u ^ swz) << 4), onehot8(q2.z, q2.w, lrep));
-          st_shared_v4(dst + ((6u ^ swz) << 4), onehot8(q3.x, q3.y, lrep));
-          st_shared_v4(dst + ((7u ^ swz) << 4), onehot8(q3.z, q3.w, lrep));
+        if (valid) {
+          st_shared_v4(dst + ((0u ^ swz) << 4), onehot8_set(q0.x, q0.y, lpair));
+          st_shared_v4(dst + ((1u ^ swz) << 4), onehot8_set(q0.z, q0.w, lpair));
+          st_shared_v4(dst + ((2u ^ swz) << 4), onehot8_set(q1.x, q1.y, lpair));
+          st_shared_v4(dst + ((3u ^ swz) << 4), onehot8_set(q1.z, q1.w, lpair));
+          st_shared_v4(dst + ((4u ^ swz) << 4), onehot8_set(q2.x, q2.y, lpair));
+          st_shared_v4(dst + ((5u ^ swz) << 4), onehot8_set(q2.z, q2.w, lpair));
+          st_shared_v4(dst + ((6u ^ swz) << 4), onehot8_set(q3.x, q3.y, lpair));
+          st_shared_v4(dst + ((7u ^ swz) << 4), onehot8_set(q3.z, q3.w, lpair));
         } else if (write) {
 #pragma unroll
           for (uint32_t q = 0; q < 8; ++q) st_shared_v4(dst + ((q ^ swz) << 4), zero4);
