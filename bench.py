@@ -359,7 +359,8 @@ def _serve(reqs, rate, seed, gens, R, P):
             "tick_ms_max": st["tick_ms_max"],
             "admission_wait_ms_mean": st["admit_wait_ms_total"] / max(1, st["admitted"]),
             "admission_wait_ms_max": st["admit_wait_ms_max"],
-            "instance_setup_ms_mean": st["admit_ms_total"] / max(1, st["admitted"])}
+            "instance_setup_ms_mean": st["admit_ms_total"] / max(1, st["admitted"]),
+            "tick_graph_builds": st["graph_builds"]}
 
 
 def rel_error_sample(gi, inst, count=64, seed=99):

@@ -293,7 +293,9 @@ int usaphmp_ga_run_profiled(usaphmp_t h, int32_t generations, void* stream, doub
  * alone exceeds the budget finishes with USAPHMP_EBUSY.  Each
  * usaphmp_server_step admits what fits, then enqueues up to 8 generations
  * (§5) of every running request -- as many as every one of them still needs,
- * at most 8 -- with one launch per kernel and generation over all of them.
+ * at most 8 -- with one launch per kernel and generation over all of them,
+ * replayed from a CUDA graph that is captured again only when the running
+ * set changes.
  * A request's result does not depend on which other requests ran beside it.
  * The step does no device-memory management and waits for no request: a
  * worker thread of the server makes each admitted request's instance
@@ -320,14 +322,16 @@ int usaphmp_server_step(usaphmp_server_t s, int32_t* n_active, int32_t* n_pendin
 
 /* Counters since the server was made: ticks and their host wall time (total
  * and largest, ms), requests admitted into the running set, their wait from
- * submission to joining it (total and largest, ms), and the worker's time
- * making their instances (total, ms). */
+ * submission to joining it (total and largest, ms), the worker's time making
+ * their instances (total, ms), and the ticks that captured their generation
+ * graph anew. */
 typedef struct {
   int64_t ticks;
   double tick_ms_total, tick_ms_max;
   int64_t admitted;
   double admit_wait_ms_total, admit_wait_ms_max;
   double admit_ms_total;
+  int64_t graph_builds;   /* ticks that captured their generations anew (the others replayed) */
 } usaphmp_server_counters;
 int usaphmp_server_stats(usaphmp_server_t s, usaphmp_server_counters* out);
 

@@ -56,7 +56,8 @@ class Info(ctypes.Structure):
 
 class ServerStats(ctypes.Structure):
     _fields_ = [("ticks", c_i64), ("tick_ms_total", c_f64), ("tick_ms_max", c_f64), ("admitted", c_i64),
-                ("admit_wait_ms_total", c_f64), ("admit_wait_ms_max", c_f64), ("admit_ms_total", c_f64)]
+                ("admit_wait_ms_total", c_f64), ("admit_wait_ms_max", c_f64), ("admit_ms_total", c_f64),
+                ("graph_builds", c_i64)]
 
 
 class UsaphmpError(RuntimeError):

@@ -82,7 +82,8 @@ struct Job {
 
 // Generations a step runs for the running requests at most: fewer host round
 // trips per generation at the cost of admitting new requests only between
-// steps.
+// steps.  A step's generations are replayed from a CUDA graph of the running
+// set (captured again only when the set changes).
 constexpr int kGensPerTick = 8;
 
 struct usaphmp_server_s {
@@ -94,6 +95,9 @@ struct usaphmp_server_s {
   Task* d_tasks = nullptr;
   std::vector<Task> h_tasks;
   bool tasks_dirty = true;                 // the device task table no longer matches `active`
+  cudaGraphExec_t gexec = nullptr;         // the tick's generations for the current running set
+  bool graph_valid = false;
+  int graph_k = 0;
   cudaEvent_t tick_ev[2] = {nullptr, nullptr};
   int64_t ticks = 0;
   std::deque<Request*> pending;            // tick thread only
@@ -385,23 +389,51 @@ int usaphmp_server_step(usaphmp_server_t s, int32_t* n_active, int32_t* n_pendin
                                             cudaMemcpyHostToDevice, s->stream);
       if (e != cudaSuccess) return report_error(USAPHMP_ECUDA, std::string("task upload: ") + cudaGetErrorString(e));
       s->tasks_dirty = false;
+      s->graph_valid = false;
     }
     int k = kGensPerTick;
     for (Request* r : s->active) {
       tc = handle_uses_tc(r->h);
       k = std::min(k, r->G - r->gens);
     }
-    const TaskSet ts{s->d_tasks, s->h_tasks.data(), (int)s->h_tasks.size()};
-    for (int g = 0; g < k; ++g) {
-      launch_children(ts, s->stream);
-      launch_alloc(ts, true, tc, s->stream);
-      if (tc)
-        launch_eval_tc(ts, s->num_sms, s->d_status, s->stream);
-      else
-        launch_eval_plain(ts, s->stream);
-      launch_reduce_select(ts, s->stream);
+    // The tick's generations (k x 4 launches over the running set, with
+    // programmatic edges) are captured into a CUDA graph when the running
+    // set or k changes -- the executable graph is updated in place when only
+    // its launch parameters differ -- and replayed otherwise.
+    cudaError_t e = cudaSuccess;
+    if (!s->graph_valid || s->graph_k != k) {
+      const TaskSet ts{s->d_tasks, s->h_tasks.data(), (int)s->h_tasks.size()};
+      e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        for (int g = 0; g < k; ++g) {
+          launch_children(ts, s->stream);
+          launch_alloc(ts, true, tc, s->stream);
+          if (tc)
+            launch_eval_tc(ts, s->num_sms, s->d_status, s->stream);
+          else
+            launch_eval_plain(ts, s->stream);
+          launch_reduce_select(ts, s->stream);
+        }
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(s->stream, &g);
+        if (e == cudaSuccess) {
+          cudaGraphExecUpdateResultInfo info;
+          if (!s->gexec || cudaGraphExecUpdate(s->gexec, g, &info) != cudaSuccess) {
+            cudaGetLastError();   // an update that does not apply is not an error
+            if (s->gexec) cudaGraphExecDestroy(s->gexec);
+            s->gexec = nullptr;
+            e = cudaGraphInstantiate(&s->gexec, g, 0);
+          }
+          cudaGraphDestroy(g);
+        }
+      }
+      if (e != cudaSuccess)
+        return report_error(USAPHMP_ECUDA, std::string("tick graph: ") + cudaGetErrorString(e));
+      s->graph_valid = true;
+      s->graph_k = k;
+      s->stats.graph_builds += 1;
     }
-    cudaError_t e = cudaGetLastError();
+    e = cudaGraphLaunch(s->gexec, s->stream);
     if (e == cudaSuccess) e = cudaEventRecord(slot_ev, s->stream);
     if (e != cudaSuccess) return report_error(USAPHMP_ECUDA, std::string("generation launch: ") + cudaGetErrorString(e));
     ++s->ticks;
@@ -527,6 +559,7 @@ void usaphmp_server_destroy(usaphmp_server_t s) {
   for (Request* r : s->pending) delete r;
   for (cudaEvent_t& ev : s->tick_ev)
     if (ev) cudaEventDestroy(ev);
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
   if (s->d_tasks) cudaFree(s->d_tasks);
   if (s->d_status) cudaFree(s->d_status);
   if (s->pool) {
