@@ -151,7 +151,9 @@ def check(rc):
 
 
 def _ptr(a):
-    return a.ctypes.data_as(c_vp)
+    # the buffer's address as an int (c_void_p arguments accept it; cheaper
+    # than building a ctypes pointer object on every call)
+    return a.__array_interface__["data"][0]
 
 
 def debug_fail_allocations(after):
