@@ -32,6 +32,8 @@
 // of one tile overlap the MMAs of the next.  Every wait is bounded: after
 // kTimeoutNs the kernel raises kStatusTimeout, drains its own copies and
 // MMAs, frees TMEM and returns.
+#include <type_traits>
+
 #include "usaphmp.h"
 
 #include "common.cuh"
@@ -246,53 +248,117 @@ struct EpiArgs {
   float* out;
 };
 
-// Epilogue of one warp over its chromosomes [cb, ce), one at a time: the p
-// accumulator columns of the chromosome (TMEM loads of WID columns), the
-// row's p factors Chub_b[s_b(row)][0..p) as 16-byte vectors, one fma chain
-// and a warp butterfly over the 32 rows.  Rows past n hold zeros (the TMA
-// fills them), so they add nothing.
+// The sums over the warp's 32 rows of 8 chromosomes at a time, taken as the
+// chromosomes' values arrive (a transposed butterfly).  Chromosomes 2i and
+// 2i + 1 meet at the step over lane bit 16: each lane keeps one of the two
+// and adds its partner's copy of it; the pairs (0,1), (2,3) of those meet at
+// bit 8, the two halves at bit 4, then bits 2 and 1 as usual.  Every
+// chromosome's total is the same tree of pairwise sums as the one-value
+// butterfly (lanes l, l^16, then l^8, ...), so it has the same bits, in 9
+// shuffles instead of 40, with at most four partial sums live.  Lane l ends
+// with the total of chromosome 4 b4 + 2 b8 + b16 (b the bits of l); lanes
+// with l % 4 == 0 store it.
+struct Tree8 {
+  float prev, w0, x0, x1;
+};
+
+__device__ __forceinline__ float tree_pair(float lo, float hi, bool b, int m) {
+  const float send = b ? lo : hi;
+  return (b ? hi : lo) + __shfl_xor_sync(0xffffffffu, send, m);
+}
+
+// Feeds chromosome bs + jj's per-lane value (0 past the warp's range).
+template <int JJ>
+__device__ __forceinline__ void tree_add(Tree8& t, int lane, float v) {
+  if constexpr ((JJ & 1) == 0) {
+    t.prev = v;
+  } else {
+    const float w = tree_pair(t.prev, v, lane & 16, 16);
+    if constexpr ((JJ & 2) == 0) {
+      t.w0 = w;
+    } else {
+      const float x = tree_pair(t.w0, w, lane & 8, 8);
+      if constexpr (JJ < 4) t.x0 = x; else t.x1 = x;
+    }
+  }
+}
+
+__device__ __forceinline__ void tree_store(const EpiArgs& a, int bs, const Tree8& t) {
+  const int lane = a.lane;
+  float y = tree_pair(t.x0, t.x1, lane & 4, 4);
+  y += __shfl_xor_sync(0xffffffffu, y, 2);
+  y += __shfl_xor_sync(0xffffffffu, y, 1);
+  const int j = ((lane & 4) ? 4 : 0) + ((lane & 8) ? 2 : 0) + ((lane & 16) ? 1 : 0);
+  if ((lane & 3) == 0 && bs + j < a.ce) a.out[bs + j] = y;
+}
+
+// Unrolls f(integral_constant<jj>) for jj = 0..7.
+template <int JJ = 0, class F>
+__device__ __forceinline__ void unroll8(F&& f) {
+  if constexpr (JJ < 8) {
+    f(std::integral_constant<int, JJ>{});
+    unroll8<JJ + 1>(f);
+  }
+}
+
+// The row's slot in chromosome c and its factors Chub_c[s_c(row)][0..p).
+__device__ __forceinline__ const float* epi_factors(const EpiArgs& a, int c) {
+  const int p = a.p;
+  const int sr = !a.rvalid ? 0
+                 : a.use_tbl ? min((int)a.tbl[(c - a.cb) * 32 + a.lane], p - 1)
+                             : min((int)__ldg(a.slot + (long long)c * a.ns + a.row), p - 1);
+  return a.fbase + c * a.cst + sr * a.hst;
+}
+
+// Epilogue of one warp over its chromosomes [cb, ce), 8 at a time: per
+// chromosome the p accumulator columns (TMEM loads of WID columns), the row's
+// p factors as 16-byte vectors and one fma chain, fed to a Tree8.  Rows
+// past n hold zeros (the TMA fills them), so they add nothing.
 template <int WID>
 __device__ __forceinline__ void epi_chromosomes(const EpiArgs& a) {
   constexpr int LMAX = 32;
   const int p = a.p;
-  for (int c = a.cb; c < a.ce; ++c) {
-    const int sr = !a.rvalid ? 0
-                   : a.use_tbl ? min((int)a.tbl[(c - a.cb) * 32 + a.lane], p - 1)
-                               : min((int)__ldg(a.slot + (long long)c * a.ns + a.row), p - 1);
-    const float* frow = a.fbase + c * a.cst + sr * a.hst;
-    float acc = 0.f;
-    for (int l0 = 0; l0 < p; l0 += LMAX) {
-      const int nl = min(LMAX, p - l0);
-      uint32_t v[LMAX];
+  for (int bs = a.cb; bs < a.ce; bs += 8) {
+    Tree8 t;
+    unroll8([&](auto J) {
+      constexpr int jj = decltype(J)::value;
+      const int c = bs + jj;
+      float acc = 0.f;
+      if (c < a.ce) {
+        const float* frow = epi_factors(a, c);
+        for (int l0 = 0; l0 < p; l0 += LMAX) {
+          const int nl = min(LMAX, p - l0);
+          uint32_t v[LMAX];
 #pragma unroll
-      for (int l = 0; l < LMAX; ++l) v[l] = 0u;
-      const uint32_t ta = a.taddr + (uint32_t)(c * p + l0);
+          for (int l = 0; l < LMAX; ++l) v[l] = 0u;
+          const uint32_t ta = a.taddr + (uint32_t)(c * p + l0);
 #pragma unroll
-      for (int l = 0; l < LMAX; l += WID) {
-        if (l < nl) {
-          if constexpr (WID == 4)
-            ptx::tmem_ld_32x4(ta + l, v[l], v[l + 1], v[l + 2], v[l + 3]);
-          else if constexpr (WID == 2)
-            ptx::tmem_ld_32x2(ta + l, v[l], v[l + 1]);
-          else
-            ptx::tmem_ld_32x1(ta + l, v[l]);
+          for (int l = 0; l < LMAX; l += WID) {
+            if (l < nl) {
+              if constexpr (WID == 4)
+                ptx::tmem_ld_32x4(ta + l, v[l], v[l + 1], v[l + 2], v[l + 3]);
+              else if constexpr (WID == 2)
+                ptx::tmem_ld_32x2(ta + l, v[l], v[l + 1]);
+              else
+                ptx::tmem_ld_32x1(ta + l, v[l]);
+            }
+          }
+          ptx::tmem_ld_wait32(v);
+#pragma unroll
+          for (int q = 0; q < LMAX / 4; ++q) {
+            if (4 * q < nl) {
+              const float4 f = *reinterpret_cast<const float4*>(frow + l0 + 4 * q);
+              acc = fmaf(__uint_as_float(v[4 * q]), f.x, acc);
+              if (4 * q + 1 < nl) acc = fmaf(__uint_as_float(v[4 * q + 1]), f.y, acc);
+              if (4 * q + 2 < nl) acc = fmaf(__uint_as_float(v[4 * q + 2]), f.z, acc);
+              if (4 * q + 3 < nl) acc = fmaf(__uint_as_float(v[4 * q + 3]), f.w, acc);
+            }
+          }
         }
       }
-      ptx::tmem_ld_wait32(v);
-#pragma unroll
-      for (int q = 0; q < LMAX / 4; ++q) {
-        if (4 * q < nl) {
-          const float4 t = *reinterpret_cast<const float4*>(frow + l0 + 4 * q);
-          acc = fmaf(__uint_as_float(v[4 * q]), t.x, acc);
-          if (4 * q + 1 < nl) acc = fmaf(__uint_as_float(v[4 * q + 1]), t.y, acc);
-          if (4 * q + 2 < nl) acc = fmaf(__uint_as_float(v[4 * q + 2]), t.z, acc);
-          if (4 * q + 3 < nl) acc = fmaf(__uint_as_float(v[4 * q + 3]), t.w, acc);
-        }
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (a.lane == 0) a.out[c] = acc;
+      tree_add<jj>(t, a.lane, acc);
+    });
+    tree_store(a, bs, t);
   }
 }
 
@@ -318,12 +384,9 @@ __device__ __forceinline__ void epi_issue(const EpiArgs& a, int c, uint32_t (&v)
 }
 
 template <int LM>
-__device__ __forceinline__ void epi_finish(const EpiArgs& a, int c, const uint32_t (&v)[LM]) {
+__device__ __forceinline__ float epi_dot(const EpiArgs& a, int c, const uint32_t (&v)[LM]) {
   const int p = a.p;
-  const int sr = !a.rvalid ? 0
-                 : a.use_tbl ? min((int)a.tbl[(c - a.cb) * 32 + a.lane], p - 1)
-                             : min((int)__ldg(a.slot + (long long)c * a.ns + a.row), p - 1);
-  const float* frow = a.fbase + c * a.cst + sr * a.hst;
+  const float* frow = epi_factors(a, c);
   float acc = 0.f;
 #pragma unroll
   for (int q = 0; q < LM / 4; ++q) {
@@ -335,9 +398,7 @@ __device__ __forceinline__ void epi_finish(const EpiArgs& a, int c, const uint32
       if (4 * q + 3 < p) acc = fmaf(__uint_as_float(v[4 * q + 3]), t.w, acc);
     }
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (a.lane == 0) a.out[c] = acc;
+  return acc;
 }
 
 template <int WID, int LM>
@@ -347,18 +408,27 @@ __device__ __forceinline__ void epi_chromosomes_pipe(const EpiArgs& a) {
 #pragma unroll
   for (int l = 0; l < LM; ++l) va[l] = vb[l] = 0u;
   epi_issue<WID, LM>(a, a.cb, va);
-  int c = a.cb;
-  for (; c + 1 < a.ce; c += 2) {
-    ptx::tmem_ld_wait_n<LM>(va);
-    epi_issue<WID, LM>(a, c + 1, vb);
-    epi_finish<LM>(a, c, va);
-    ptx::tmem_ld_wait_n<LM>(vb);
-    if (c + 2 < a.ce) epi_issue<WID, LM>(a, c + 2, va);
-    epi_finish<LM>(a, c + 1, vb);
-  }
-  if (c < a.ce) {
-    ptx::tmem_ld_wait_n<LM>(va);
-    epi_finish<LM>(a, c, va);
+  // batches start at cb + 8k, so an even offset in a batch is always in va
+  for (int bs = a.cb; bs < a.ce; bs += 8) {
+    Tree8 t;
+    unroll8([&](auto J) {
+      constexpr int jj = decltype(J)::value;
+      const int c = bs + jj;
+      float d = 0.f;
+      if (c < a.ce) {
+        if constexpr ((jj & 1) == 0) {
+          ptx::tmem_ld_wait_n<LM>(va);
+          if (c + 1 < a.ce) epi_issue<WID, LM>(a, c + 1, vb);
+          d = epi_dot<LM>(a, c, va);
+        } else {
+          ptx::tmem_ld_wait_n<LM>(vb);
+          if (c + 1 < a.ce) epi_issue<WID, LM>(a, c + 1, va);
+          d = epi_dot<LM>(a, c, vb);
+        }
+      }
+      tree_add<jj>(t, a.lane, d);
+    });
+    tree_store(a, bs, t);
   }
 }
 
