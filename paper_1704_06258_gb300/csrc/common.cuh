@@ -41,8 +41,12 @@ __host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m *
 __device__ __forceinline__ float access_term(float chi, float Oi, float cih, float delta, float Di, float chi_i) {
   return __fmaf_rn(__fmul_rn(delta, Di), chi_i, __fmul_rn(__fmul_rn(chi, Oi), cih));
 }
-__host__ __device__ inline int chub_hstride(int p) { return 4 * (((p + 3) / 4) | 1); }
-__host__ __device__ inline int chub_cstride(int p) { return p * chub_hstride(p); }
+// A chromosome's p x p hub-cost table (chub): row k at k * hstride floats.
+// The odd row stride puts 32 different rows on 32 different shared-memory
+// banks, so a warp whose lanes read one column of rows s(lane) never
+// conflicts; tables start 16 bytes apart (whole bulk copies).
+__host__ __device__ inline int chub_hstride(int p) { return p | 1; }
+__host__ __device__ inline int chub_cstride(int p) { return round_up(p * chub_hstride(p), 4); }
 
 // The plain evaluator keeps one p x p hub-cost table and the slot codes of a
 // chromosome in shared memory; past this budget (p above about 220) it reads

@@ -312,8 +312,9 @@ __device__ __forceinline__ const float* epi_factors(const EpiArgs& a, int c) {
 
 // Epilogue of one warp over its chromosomes [cb, ce), 8 at a time: per
 // chromosome the p accumulator columns (TMEM loads of WID columns), the row's
-// p factors as 16-byte vectors and one fma chain, fed to a Tree8.  Rows
-// past n hold zeros (the TMA fills them), so they add nothing.
+// p factors (one load each, free of bank conflicts by the odd row stride)
+// and one fma chain, fed to a Tree8.  Rows past n hold zeros (the TMA fills
+// them), so they add nothing.
 template <int WID>
 __device__ __forceinline__ void epi_chromosomes(const EpiArgs& a) {
   constexpr int LMAX = 32;
@@ -345,15 +346,8 @@ __device__ __forceinline__ void epi_chromosomes(const EpiArgs& a) {
           }
           ptx::tmem_ld_wait32(v);
 #pragma unroll
-          for (int q = 0; q < LMAX / 4; ++q) {
-            if (4 * q < nl) {
-              const float4 f = *reinterpret_cast<const float4*>(frow + l0 + 4 * q);
-              acc = fmaf(__uint_as_float(v[4 * q]), f.x, acc);
-              if (4 * q + 1 < nl) acc = fmaf(__uint_as_float(v[4 * q + 1]), f.y, acc);
-              if (4 * q + 2 < nl) acc = fmaf(__uint_as_float(v[4 * q + 2]), f.z, acc);
-              if (4 * q + 3 < nl) acc = fmaf(__uint_as_float(v[4 * q + 3]), f.w, acc);
-            }
-          }
+          for (int l = 0; l < LMAX; ++l)
+            if (l < nl) acc = fmaf(__uint_as_float(v[l]), frow[l0 + l], acc);
         }
       }
       tree_add<jj>(t, a.lane, acc);
@@ -389,15 +383,8 @@ __device__ __forceinline__ float epi_dot(const EpiArgs& a, int c, const uint32_t
   const float* frow = epi_factors(a, c);
   float acc = 0.f;
 #pragma unroll
-  for (int q = 0; q < LM / 4; ++q) {
-    if (4 * q < p) {
-      const float4 t = *reinterpret_cast<const float4*>(frow + 4 * q);
-      acc = fmaf(__uint_as_float(v[4 * q]), t.x, acc);
-      if (4 * q + 1 < p) acc = fmaf(__uint_as_float(v[4 * q + 1]), t.y, acc);
-      if (4 * q + 2 < p) acc = fmaf(__uint_as_float(v[4 * q + 2]), t.z, acc);
-      if (4 * q + 3 < p) acc = fmaf(__uint_as_float(v[4 * q + 3]), t.w, acc);
-    }
-  }
+  for (int l = 0; l < LM; ++l)
+    if (l < p) acc = fmaf(__uint_as_float(v[l]), frow[l], acc);
   return acc;
 }
 
