@@ -563,8 +563,7 @@ def run_ours(args):
         gi.set_params(islands=ISLANDS, island_size=ISLAND, n1=10, path=PATH_SPLIT_BF16)
         folded = bool(gi.info()["tc_folded"])
         if args.tile:                    # a fixed tile shape (profiling runs)
-            nt, st, ra = (int(v) for v in args.tile.split(","))
-            gi.set_tile(nt, st, ra)
+            gi.set_tile(*(int(v) for v in args.tile.split(",")))
             tile = dict(gi.get_tile(), fixed=True)
         else:
             tile = gi.autotune(reps=20)  # tile shape of the TC kernel, chosen before any timing
@@ -708,7 +707,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--tile", default="", help="fixed TC tile shape ntile,stages,raster instead of the autotuner")
+    ap.add_argument("--tile", default="", help="fixed TC tile shape ntile,stages,raster[,pair] instead of the autotuner")
     ap.add_argument("--serve", type=int, default=512, help="serving requests (0 = skip the serving leg)")
     ap.add_argument("--large", type=int, default=1, help="also time the n=6000 configuration (0 = skip)")
     ap.add_argument("--legs", choices=["all", "split"], default="all",

@@ -361,9 +361,14 @@ void usaphmp_server_destroy(usaphmp_server_t s);
  * one-hot allocation matrices of the population in tiles of 128 rows x
  * ntile columns; a tile holds floor(ntile / p) whole chromosomes.  Shape:
  *   ntile   64, 128 or 256 (>= p)
- *   stages  2..4 shared-memory pipeline stages (ntile 256: at most 3)
+ *   stages  2..4 shared-memory pipeline stages (ntile 256: at most 3 with
+ *           pair 0)
  *   raster  0: the persistent CTAs walk the column tiles of one row block of
  *           W first; 1: the row blocks of one column tile first.
+ *   pair    0: one CTA per MMA (M = 128); 1: clusters of two CTAs on
+ *           neighbouring SMs run each MMA over two row blocks (M = 256,
+ *           tcgen05 cta_group::2), each CTA staging its own row block of W
+ *           and half of the one-hot columns.
  * The shape changes speed only: fitness values are bit-identical for every
  * shape.  Default {256, 3, 0}.  A handle's shape applies to its own
  * evaluations and generations; the server uses the default. */
@@ -371,6 +376,7 @@ typedef struct {
   int32_t ntile;
   int32_t stages;
   int32_t raster;
+  int32_t pair;
 } usaphmp_tile;
 
 /* USAPHMP_EINVAL (nothing changed) for a shape outside the list above or

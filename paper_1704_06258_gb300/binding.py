@@ -46,7 +46,7 @@ class Result(ctypes.Structure):
 
 
 class Tile(ctypes.Structure):
-    _fields_ = [("ntile", c_i32), ("stages", c_i32), ("raster", c_i32)]
+    _fields_ = [("ntile", c_i32), ("stages", c_i32), ("raster", c_i32), ("pair", c_i32)]
 
 
 class Info(ctypes.Structure):
@@ -175,7 +175,7 @@ def rescore_fp64_noalloc(n, p, B, W_ptr, C_ptr, chi, alpha, delta, hubs_ptr, slo
 
 
 def _tile_dict(t):
-    return {"ntile": int(t.ntile), "stages": int(t.stages), "raster": int(t.raster)}
+    return {"ntile": int(t.ntile), "stages": int(t.stages), "raster": int(t.raster), "pair": int(t.pair)}
 
 
 def tile_cache_lookup(path, device, n, p, B):
@@ -192,9 +192,9 @@ def tile_cache_lookup(path, device, n, p, B):
     return d
 
 
-def tile_cache_store(path, device, n, p, B, ntile, stages, raster, ms):
+def tile_cache_store(path, device, n, p, B, ntile, stages, raster, ms, pair=0):
     """usaphmp_tile_cache_store."""
-    t = Tile(ntile, stages, raster)
+    t = Tile(ntile, stages, raster, pair)
     check(lib().usaphmp_tile_cache_store(os.fsencode(path), device.encode(), n, p, B, ctypes.byref(t), ms))
 
 
@@ -250,9 +250,9 @@ class Instance:
         prm = Params(**cur)
         check(lib().usaphmp_set_params(self.h, ctypes.byref(prm)))
 
-    def set_tile(self, ntile, stages, raster):
+    def set_tile(self, ntile, stages, raster, pair=0):
         """usaphmp_set_tile: tile shape of the tensor-core evaluator."""
-        t = Tile(ntile, stages, raster)
+        t = Tile(ntile, stages, raster, pair)
         check(lib().usaphmp_set_tile(self.h, ctypes.byref(t)))
 
     def info(self):

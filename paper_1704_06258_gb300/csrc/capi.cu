@@ -689,9 +689,10 @@ int usaphmp_set_tile(usaphmp_t h, const usaphmp_tile* tile) {
   t.ntile = tile->ntile;
   t.stages = tile->stages;
   t.raster = tile->raster;
+  t.pair = tile->pair;
   if (!tc_tile_fits(t, h->p))
     return fail(USAPHMP_EINVAL, "tile shape: ntile in {64, 128, 256} and >= p, stages 2..4 within shared memory "
-                                "(ntile 256: at most 3), raster 0 or 1");
+                                "(ntile 256: at most 3, or 4 with pair 1), raster 0 or 1, pair 0 or 1");
   h->tile = t;
   drop_graph(h);
   return USAPHMP_OK;
@@ -702,6 +703,7 @@ int usaphmp_get_tile(usaphmp_t h, usaphmp_tile* tile) {
   tile->ntile = h->tile.ntile;
   tile->stages = h->tile.stages;
   tile->raster = h->tile.raster;
+  tile->pair = h->tile.pair;
   return USAPHMP_OK;
 }
 
@@ -740,15 +742,16 @@ int usaphmp_autotune(usaphmp_t h, int32_t reps, const char* cache_path, usaphmp_
   RET(enqueue_generation(h, s));
   h->ga_ready = false;
   std::vector<TcTile> cands{TcTile{}};
-  for (int nt : {256, 128, 64})
-    for (int st : {2, 3, 4})
-      for (int ra : {0, 1}) {
-        TcTile t;
-        t.ntile = nt; t.stages = st; t.raster = ra;
-        const TcTile d{};
-        const bool is_default = nt == d.ntile && st == d.stages && ra == d.raster;
-        if (!is_default && tc_tile_fits(t, h->p)) cands.push_back(t);
-      }
+  for (int pr : {0, 1})
+    for (int nt : {256, 128, 64})
+      for (int st : {2, 3, 4})
+        for (int ra : {0, 1}) {
+          TcTile t;
+          t.ntile = nt; t.stages = st; t.raster = ra; t.pair = pr;
+          const TcTile d{};
+          const bool is_default = nt == d.ntile && st == d.stages && ra == d.raster && pr == d.pair;
+          if (!is_default && tc_tile_fits(t, h->p)) cands.push_back(t);
+        }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CK(cudaEventCreate(&e0));
   cudaError_t ce = cudaEventCreate(&e1);
@@ -781,7 +784,7 @@ int usaphmp_autotune(usaphmp_t h, int32_t reps, const char* cache_path, usaphmp_
   h->tile = best;
   drop_graph(h);
   if (cache_path) {
-    const usaphmp_tile t{best.ntile, best.stages, best.raster};
+    const usaphmp_tile t{best.ntile, best.stages, best.raster, best.pair};
     RET(usaphmp_tile_cache_store(cache_path, device.c_str(), h->n, h->p, B, &t, best_ms));
   }
   if (chosen_ms) *chosen_ms = best_ms;

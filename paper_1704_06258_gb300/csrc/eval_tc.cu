@@ -54,15 +54,21 @@ constexpr int kTblChrom = 86;                              // chromosomes of a t
 constexpr int kTblWarpChrom = kTblChrom / 2;               // per epilogue warp: u8 [8 warps][43][32 rows]
 constexpr uint32_t kTblBytes = kEpiWarps * kTblWarpChrom * 32;
 constexpr int kNumBars = 3 * kMaxStages + 7;
+// top of shared memory: the barriers, the TMEM address and abort flag, then
+// (16-byte aligned) the pair mode's signal slots: one 16-byte landing slot
+// per stage and one source slot
+constexpr uint32_t kSigOff = (8 * kNumBars + 8 + 15) & ~15u;
+constexpr uint32_t kTopBytes = kSigOff + 16 * (kMaxStages + 1);
 constexpr uint32_t kSmemBytes = 232448;                    // dynamic shared memory of one CTA (227 KB)
 constexpr uint32_t kUsable = kSmemBytes - 1024;            // after aligning the base to 1024
 constexpr uint64_t kTimeoutNs = 2000000000ull;
 
 // Shared-memory layout of a tile shape: `stages` stages of [A_hi | A_lo | B]
-// (B = ntile rows x 128 bytes), then the slab for the tile's Chub tables
-// (whatever room is left), the slot-code table and the barriers at the top.
+// (B = ntile rows x 128 bytes; in pair mode this CTA's half, ntile / 2
+// rows), then the slab for the tile's Chub tables (whatever room is left),
+// the slot-code table and the barriers at the top.
 struct Lay {
-  int ntile, stages, raster;
+  int ntile, stages, raster, pair;
   uint32_t stage_bytes, slab_off, slab_bytes, tbl_off, bar_off;
   bool ok;
 };
@@ -72,12 +78,14 @@ __host__ __device__ inline Lay lay_of(const TcTile& t) {
   L.ntile = t.ntile;
   L.stages = t.stages;
   L.raster = t.raster;
-  L.stage_bytes = 2 * A_BYTES + (uint32_t)t.ntile * BK * 2;
-  L.bar_off = (kUsable - (8 * kNumBars + 8)) & ~15u;
+  L.pair = t.pair;
+  L.stage_bytes = 2 * A_BYTES + (uint32_t)(t.pair ? t.ntile / 2 : t.ntile) * BK * 2;
+  L.bar_off = (kUsable - kTopBytes) & ~15u;
   L.tbl_off = (L.bar_off - kTblBytes) & ~15u;
   L.slab_off = (uint32_t)t.stages * L.stage_bytes;
   L.ok = (t.ntile == 64 || t.ntile == 128 || t.ntile == 256) && t.stages >= 2 && t.stages <= kMaxStages &&
-         (t.raster == 0 || t.raster == 1) && L.slab_off <= L.tbl_off;
+         (t.raster == 0 || t.raster == 1) && (t.pair == 0 || (t.pair == 1 && t.ntile >= 64)) &&
+         L.slab_off <= L.tbl_off;
   L.slab_bytes = L.ok ? (L.tbl_off - L.slab_off) & ~15u : 0;
   return L;
 }
@@ -92,16 +100,29 @@ struct Bars {
   __device__ uint32_t drain() const { return base + 8 * (3 * kMaxStages + 4); }
   __device__ uint32_t slab_full() const { return base + 8 * (3 * kMaxStages + 5); }
   __device__ uint32_t slab_empty() const { return base + 8 * (3 * kMaxStages + 6); }
+  __device__ uint32_t sig(int s) const { return base + kSigOff + 16 * s; }
+  __device__ uint32_t sig_src() const { return base + kSigOff + 16 * kMaxStages; }
 };
 
 // Single-thread bounded wait.  Returns false on timeout or when another role
 // has already aborted.
+// kCluster: acquire at cluster scope (barriers the other CTA of a pair
+// arrives on).
+template <bool kCluster = false>
+__device__ __forceinline__ bool try_wait(uint32_t bar, uint32_t parity) {
+  if constexpr (kCluster)
+    return ptx::mbar_try_wait_cluster(bar, parity);
+  else
+    return ptx::mbar_try_wait(bar, parity);
+}
+
+template <bool kCluster = false>
 __device__ __forceinline__ bool wait_one(uint32_t bar, uint32_t parity, volatile int* abort_flag, uint32_t* status,
                                          uint64_t limit_ns = kTimeoutNs) {
-  if (ptx::mbar_try_wait(bar, parity)) return true;
+  if (try_wait<kCluster>(bar, parity)) return true;
   const uint64_t t0 = ptx::globaltimer();
   for (uint32_t i = 1;; ++i) {
-    if (ptx::mbar_try_wait(bar, parity)) return true;
+    if (try_wait<kCluster>(bar, parity)) return true;
     if ((i & 255u) == 0) {
       if (*abort_flag) return false;
       if (ptx::globaltimer() - t0 > limit_ns) {
@@ -121,11 +142,12 @@ __device__ void wait_drain(uint32_t bar, uint32_t parity) {
 }
 
 // Warp-collective bounded wait: every lane returns the same answer.
+template <bool kCluster = false>
 __device__ __forceinline__ bool wait_warp(uint32_t bar, uint32_t parity, volatile int* abort_flag, uint32_t* status,
                                           uint64_t limit_ns = kTimeoutNs) {
   const uint64_t t0 = ptx::globaltimer();
   for (uint32_t i = 0;; ++i) {
-    const bool ok = ptx::mbar_try_wait(bar, parity);
+    const bool ok = try_wait<kCluster>(bar, parity);
     if (__all_sync(0xffffffffu, ok)) return true;
     if ((i & 255u) == 255u) {
       int stop = 0;
@@ -172,36 +194,43 @@ struct Ring {
 };
 
 struct TileRef {
-  int task, m, nb;
+  int task, m0, m, nb;   // m0: first row block of the unit; m: this CTA's row block
 };
 
-// Tile g of the launch -> (task, row block m, column tile nb).  Raster 0
-// walks the column tiles of one row block first (CTAs running side by side
-// share the W stripe), raster 1 the row blocks of one column tile first
-// (they share the chromosomes' slot codes and hub tables).
-__device__ __forceinline__ TileRef decode_tile(const TaskParam& tp, int g, const Lay& L) {
+// Tile g of the launch -> (task, row unit, column tile nb).  A row unit is
+// one row block, or two (2u, 2u + 1) in pair mode, where CTA rank r of the
+// pair takes row block 2u + r.  Raster 0 walks the column tiles of one row
+// unit first (CTAs running side by side share the W stripe), raster 1 the
+// row units of one column tile first (they share the chromosomes' slot codes
+// and hub tables).
+__device__ __forceinline__ TileRef decode_tile(const TaskParam& tp, int g, const Lay& L, int rank) {
   TileRef r;
   r.task = task_of(tp.bo, g);
   const Task& T = task_at(tp, r.task);
   const int local = g - tp.bo.o[r.task];
+  int u;
   if (L.raster == 0) {
     const int nt = geo_of(T.in.p, T.pop.B, L).nt;
-    r.m = local / nt;
-    r.nb = local - r.m * nt;
+    u = local / nt;
+    r.nb = local - u * nt;
   } else {
     const int mt = (T.in.n + BM - 1) / BM;
-    r.nb = local / mt;
-    r.m = local - r.nb * mt;
+    const int mu = L.pair ? (mt + 1) >> 1 : mt;
+    r.nb = local / mu;
+    u = local - r.nb * mu;
   }
+  r.m0 = L.pair ? 2 * u : u;
+  r.m = r.m0 + rank;
   return r;
 }
 
-// The tile a CTA takes in round r of the persistent loop: tiles rG .. rG+G-1
-// go to CTAs 0 .. G-1, and with `snake` to CTAs G-1 .. 0 in odd rounds, so
-// that over the rounds every CTA gets an even share of tiles sorted by cost
-// (row-block-major tiles of a folded W, whose K loops shorten with m).
-__device__ __forceinline__ int tile_of_round(int r, bool snake) {
-  const int G = gridDim.x, c = blockIdx.x;
+// The tile a CTA (a pair of CTAs in pair mode) takes in round r of the
+// persistent loop: tiles rG .. rG+G-1 go to slots 0 .. G-1, and with `snake`
+// to slots G-1 .. 0 in odd rounds, so that over the rounds every slot gets
+// an even share of tiles sorted by cost (row-unit-major tiles of a folded W,
+// whose K loops shorten with the row).
+__device__ __forceinline__ int tile_of_round(int r, bool snake, int pair) {
+  const int G = (int)gridDim.x >> pair, c = (int)blockIdx.x >> pair;
   return r * G + ((snake && (r & 1)) ? G - 1 - c : c);
 }
 
@@ -431,6 +460,13 @@ __device__ __forceinline__ void epi_pipe_width(const EpiArgs& a) {
 
 }  // namespace
 
+// kPair: a cluster of two CTAs per MMA (cta_group::2, M = 256).  Rank 0
+// issues every MMA and commit; the barriers it waits on (stage full, one-hot
+// full, accumulator empty) live in its shared memory and count the arrivals
+// of both CTAs (TMA bytes of both; its 8 producer warps and the signal copy
+// of rank 1's forwarder; 2 x 8 epilogue warps); its commits arrive on the
+// stage-empty and accumulator-full barriers of both CTAs.
+template <bool kPair>
 __global__ void __launch_bounds__(kThreads, 1)
     k_eval_tc(const __grid_constant__ TaskParam tp, int total_tiles, uint32_t* status, const Lay L, int snake) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -444,16 +480,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t STAGE_BYTES = L.stage_bytes;
   const uint32_t tmem_cols = 2u * (uint32_t)L.ntile;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rank = kPair ? (int)ptx::cluster_ctarank() : 0;
+  const int pshift = kPair ? 1 : 0;
+  constexpr int kPeers = kPair ? 2 : 1;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kMaxStages; ++s) {
       ptx::mbar_init(bars.full_tma(s), 1);
-      ptx::mbar_init(bars.full_oh(s), 8);                 // one arrival per producer warp
+      // one arrival per producer warp (in pair mode rank 0's barrier also
+      // waits for the 16 bytes rank 1's forwarder copies in, see below)
+      ptx::mbar_init(bars.full_oh(s), 8);
       ptx::mbar_init(bars.empty(s), 1);
     }
     for (int b = 0; b < 2; ++b) {
       ptx::mbar_init(bars.tfull(b), 1);
-      ptx::mbar_init(bars.tempty(b), kEpiWarps);          // one arrival per epilogue warp
+      ptx::mbar_init(bars.tempty(b), kEpiWarps * kPeers); // one arrival per epilogue warp
     }
     ptx::mbar_init(bars.drain(), 1);
     ptx::mbar_init(bars.slab_full(), 1);
@@ -462,11 +503,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     ptx::fence_mbar_init();
   }
   if (warp == 1) {
-    ptx::tmem_alloc(ptx::smem_u32(const_cast<uint32_t*>(tmem_holder)), tmem_cols);
-    ptx::tmem_relinquish();
+    if constexpr (kPair) {
+      ptx::tmem_alloc_pair(ptx::smem_u32(const_cast<uint32_t*>(tmem_holder)), tmem_cols);
+      ptx::tmem_relinquish_pair();
+    } else {
+      ptx::tmem_alloc(ptx::smem_u32(const_cast<uint32_t*>(tmem_holder)), tmem_cols);
+      ptx::tmem_relinquish();
+    }
   }
   ptx::tc_fence_before();
   __syncthreads();
+  // both CTAs' barriers are initialised before either arrives on the other's
+  if constexpr (kPair) ptx::cluster_sync();
   ptx::tc_fence_after();
   const uint32_t tmem = *tmem_holder;
   // barriers and TMEM are set up: now wait for the allocation kernel's output
@@ -475,61 +523,121 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------------------ TMA producer
+    // Both CTAs load their own row block of U_hi / U_lo; in pair mode the
+    // completions count on rank 0's stage barrier, whose single arrival
+    // (rank 0's) expects the bytes of both.
     int it = 0;
     Ring ring(STAGES);
     bool ok = true;
-    for (int rd = 0, g = tile_of_round(0, snake); g < total_tiles && ok; g = tile_of_round(++rd, snake)) {
-      const TileRef tr = decode_tile(tp, g, L);
+    for (int rd = 0, g = tile_of_round(0, snake, pshift); g < total_tiles && ok;
+         g = tile_of_round(++rd, snake, pshift)) {
+      const TileRef tr = decode_tile(tp, g, L, rank);
       const Task& T = task_at(tp, tr.task);
       const int nk = (T.in.n + BK - 1) / BK;
-      for (int kb = k_begin(T, tr.m); kb < nk; ++kb, ++it, ring.next()) {
+      for (int kb = k_begin(T, tr.m0); kb < nk; ++kb, ++it, ring.next()) {
         const int s = ring.s;
         if (!(ok = wait_one(bars.empty(s), ring.ph ^ 1u, abort_flag, status))) break;
         const uint32_t a_hi = base + s * STAGE_BYTES;
-        ptx::mbar_arrive_expect_tx(bars.full_tma(s), 2 * A_BYTES);
-        ptx::tma_load_2d(a_hi, T.tmap_hi, kb * BK, tr.m * BM, bars.full_tma(s));
-        ptx::tma_load_2d(a_hi + A_BYTES, T.tmap_lo, kb * BK, tr.m * BM, bars.full_tma(s));
+        if constexpr (kPair) {
+          if (rank == 0) ptx::mbar_arrive_expect_tx(bars.full_tma(s), 4 * A_BYTES);
+          const uint32_t fb = ptx::mapa(bars.full_tma(s), 0);
+          ptx::tma_load_2d_pair(a_hi, T.tmap_hi, kb * BK, tr.m * BM, fb);
+          ptx::tma_load_2d_pair(a_hi + A_BYTES, T.tmap_lo, kb * BK, tr.m * BM, fb);
+        } else {
+          ptx::mbar_arrive_expect_tx(bars.full_tma(s), 2 * A_BYTES);
+          ptx::tma_load_2d(a_hi, T.tmap_hi, kb * BK, tr.m * BM, bars.full_tma(s));
+          ptx::tma_load_2d(a_hi + A_BYTES, T.tmap_lo, kb * BK, tr.m * BM, bars.full_tma(s));
+        }
       }
     }
-    for (int j = it - STAGES < 0 ? 0 : it - STAGES; j < it; ++j)
-      wait_drain(bars.full_tma(j % STAGES), (uint32_t)(j / STAGES) & 1u);
-  } else if (warp == 1 && lane == 0) {
+    // the copies still in flight land before the CTA exits (in pair mode
+    // rank 0's barrier counts both CTAs' copies; rank 1 is held by the
+    // final cluster barrier until rank 0 has seen them land)
+    if (rank == 0)
+      for (int j = it - STAGES < 0 ? 0 : it - STAGES; j < it; ++j)
+        wait_drain(bars.full_tma(j % STAGES), (uint32_t)(j / STAGES) & 1u);
+  } else if (warp == 1 && lane == 0 && rank == 0) {
     // ------------------------------------------------------------- MMA issuer
     int tl = 0;
     Ring ring(STAGES);
     bool ok = true;
-    for (int rd = 0, g = tile_of_round(0, snake); g < total_tiles && ok; g = tile_of_round(++rd, snake), ++tl) {
-      const TileRef tr = decode_tile(tp, g, L);
+    const uint32_t peer = kPair ? 1u : 0u;
+    for (int rd = 0, g = tile_of_round(0, snake, pshift); g < total_tiles && ok;
+         g = tile_of_round(++rd, snake, pshift), ++tl) {
+      const TileRef tr = decode_tile(tp, g, L, rank);
       const Task& T = task_at(tp, tr.task);
       const int p = T.in.p;
       const Geo geo = geo_of(p, T.pop.B, L);
       const int nchrom = min(geo.cpt, T.pop.B - tr.nb * geo.cpt);
-      const uint32_t idesc = ptx::idesc_bf16_f32(BM, round_up(nchrom * p, 16));
+      const uint32_t idesc = ptx::idesc_bf16_f32(kPeers * BM, round_up(nchrom * p, 16 * kPeers));
       const int nk = (T.in.n + BK - 1) / BK;
-      const int kb0 = k_begin(T, tr.m);
+      const int kb0 = k_begin(T, tr.m0);
       const int buf = tl & 1;
       const uint32_t use = (uint32_t)(tl >> 1);
-      if (!(ok = wait_one(bars.tempty(buf), (use & 1u) ^ 1u, abort_flag, status))) break;
+      if (!(ok = wait_one<kPair>(bars.tempty(buf), (use & 1u) ^ 1u, abort_flag, status))) break;
       ptx::tc_fence_after();
       const uint32_t d = tmem + (uint32_t)(buf * L.ntile);
       for (int kb = kb0; kb < nk; ++kb, ring.next()) {
         const int s = ring.s;
         if (!(ok = wait_one(bars.full_tma(s), ring.ph, abort_flag, status))) break;
-        if (!(ok = wait_one(bars.full_oh(s), ring.ph, abort_flag, status))) break;
+        if (!(ok = wait_one<kPair>(bars.full_oh(s), ring.ph, abort_flag, status))) break;
         ptx::tc_fence_after();
         const uint32_t a_hi = base + s * STAGE_BYTES, a_lo = a_hi + A_BYTES, bt = a_lo + A_BYTES;
 #pragma unroll
         for (int k = 0; k < BK / 16; ++k) {
           const uint64_t bdesc = ptx::sw128_desc(bt + 32 * k);
-          ptx::mma_bf16(d, ptx::sw128_desc(a_hi + 32 * k), bdesc, idesc, (kb != kb0 || k != 0) ? 1u : 0u);
-          ptx::mma_bf16(d, ptx::sw128_desc(a_lo + 32 * k), bdesc, idesc, 1u);
+          const uint32_t acc = (kb != kb0 || k != 0) ? 1u : 0u;
+          if constexpr (kPair) {
+            ptx::mma_bf16_pair(d, ptx::sw128_desc(a_hi + 32 * k), bdesc, idesc, acc);
+            ptx::mma_bf16_pair(d, ptx::sw128_desc(a_lo + 32 * k), bdesc, idesc, 1u);
+          } else {
+            ptx::mma_bf16(d, ptx::sw128_desc(a_hi + 32 * k), bdesc, idesc, acc);
+            ptx::mma_bf16(d, ptx::sw128_desc(a_lo + 32 * k), bdesc, idesc, 1u);
+          }
         }
-        ptx::tc_commit(bars.empty(s));
+        if constexpr (kPair) {
+          ptx::tc_commit_pair(bars.empty(s));
+          ptx::tc_commit_pair(ptx::mapa(bars.empty(s), peer));
+        } else {
+          ptx::tc_commit(bars.empty(s));
+        }
       }
-      if (ok) ptx::tc_commit(bars.tfull(buf));
+      if (ok) {
+        if constexpr (kPair) {
+          ptx::tc_commit_pair(bars.tfull(buf));
+          ptx::tc_commit_pair(ptx::mapa(bars.tfull(buf), peer));
+        } else {
+          ptx::tc_commit(bars.tfull(buf));
+        }
+      }
     }
-    ptx::tc_commit(bars.drain());
+    if constexpr (kPair)
+      ptx::tc_commit_pair(bars.drain());
+    else
+      ptx::tc_commit(bars.drain());
     wait_drain(bars.drain(), 0);
+  } else if (kPair && warp == 1 && lane == 0) {
+    // ------------------------------------------- one-hot forwarder (rank 1)
+    // Rank 1's producer warps arrive on their own CTA's barrier; this thread
+    // passes each completed stage on to rank 0's barrier as the completion
+    // of a 16-byte copy into rank 0's shared memory (an async-proxy signal,
+    // which costs the thread nothing; a cluster-scope release arrive stalls
+    // its thread for about a K block's MMA time).  Rank 0's first producer
+    // warp adds the 16 bytes to the barrier's expected count.
+    Ring ring(STAGES);
+    bool ok = true;
+    for (int rd = 0, g = tile_of_round(0, snake, pshift); g < total_tiles && ok;
+         g = tile_of_round(++rd, snake, pshift)) {
+      const TileRef tr = decode_tile(tp, g, L, rank);
+      const Task& T = task_at(tp, tr.task);
+      const int nk = (T.in.n + BK - 1) / BK;
+      for (int kb = k_begin(T, tr.m0); kb < nk; ++kb, ring.next()) {
+        const int s = ring.s;
+        if (!(ok = wait_one(bars.full_oh(s), ring.ph, abort_flag, status))) break;
+        ptx::fence_proxy_async_smem();
+        ptx::bulk_copy_cluster(ptx::mapa(bars.sig(s), 0), bars.sig_src(), 16, ptx::mapa(bars.full_oh(s), 0));
+      }
+    }
   } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + kEpiWarps) {
     // --------------------------------------------------------------- epilogue
     const int quarter = warp & 3, half = (warp - kEpiWarp0) >> 2;
@@ -540,8 +648,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t* tbl = sm + L.tbl_off + (warp - kEpiWarp0) * (kTblWarpChrom * 32);
     const float* slab = reinterpret_cast<const float*>(sm + L.slab_off);
     int tl = 0;
-    for (int rd = 0, g = tile_of_round(0, snake); g < total_tiles; g = tile_of_round(++rd, snake), ++tl) {
-      const TileRef tr = decode_tile(tp, g, L);
+    for (int rd = 0, g = tile_of_round(0, snake, pshift); g < total_tiles;
+         g = tile_of_round(++rd, snake, pshift), ++tl) {
+      const TileRef tr = decode_tile(tp, g, L, rank);
       const Task& T = task_at(tp, tr.task);
       const int n = T.in.n, p = T.in.p, ns = T.in.ns, B = T.pop.B;
       const Geo geo = geo_of(p, B, L);
@@ -552,6 +661,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint8_t* __restrict__ slot = T.pop.slot + (long long)b0 * ns;
       const int row = tr.m * BM + quarter * 32 + lane;
       const bool rvalid = row < n;
+      // in pair mode the second row block of the last unit can lie past n:
+      // its CTA keeps step with the barriers but has no rows to sum
+      const bool live = !kPair || tr.m * BM < n;
       const bool use_tbl = nchrom <= kTblChrom;
       // this warp's chromosomes: [cb, ce)
       const int split = (nchrom + 1) >> 1;
@@ -570,7 +682,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       // slot codes of this warp's 32 rows for its chromosomes
-      if (use_tbl) {
+      if (use_tbl && live) {
         __syncwarp();
         for (int c0 = cb; c0 < ce; c0 += 8) {
           uint8_t sv[8];
@@ -594,7 +706,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       // one code path per TMEM load width (the widest that keeps every
       // column offset c*p + l aligned)
       const EpiArgs ea{taddr, cb, ce, p, hst, cst, ns, row, lane, rvalid, use_tbl, tbl, slot, fbase, out};
-      if (p <= 16) {
+      if (!live) {
+      } else if (p <= 16) {
         epi_pipe_width<16>(ea);
       } else if (p <= 24) {
         epi_pipe_width<24>(ea);
@@ -610,17 +723,83 @@ __global__ void __launch_bounds__(kThreads, 1)
       ptx::tc_fence_before();
       __syncwarp();
       if (lane == 0) {
-        ptx::mbar_arrive(bars.tempty(buf));
+        if (rank == 0)
+          ptx::mbar_arrive(bars.tempty(buf));
+        else
+          ptx::mbar_arrive_cluster(ptx::mapa(bars.tempty(buf), 0));
         ptx::mbar_arrive(bars.slab_empty());
       }
     }
-  } else if (warp >= kProdWarp0) {
+  } else if (kPair && warp >= kProdWarp0) {
+    // ------------------------------------------- one-hot producers, pair mode
+    // This CTA holds B columns [rank N/2, (rank + 1) N/2) (N = the tile's MMA
+    // width, a multiple of 32): thread t makes K half t / 128 (32 codes) of
+    // local row t % 128.  The warps arrive on their own CTA's barrier.
+    const int t = threadIdx.x - 32 * kProdWarp0;
+    const int rl = t & 127, kh = t >> 7;
+    const uint32_t swz = (uint32_t)(rl & 7);
+    const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+    Ring ring(STAGES);
+    bool ok = true;
+    for (int rd = 0, g = tile_of_round(0, snake, pshift); g < total_tiles && ok;
+         g = tile_of_round(++rd, snake, pshift)) {
+      const TileRef tr = decode_tile(tp, g, L, rank);
+      const Task& T = task_at(tp, tr.task);
+      const int n = T.in.n, p = T.in.p, ns = T.in.ns, B = T.pop.B;
+      const Geo geo = geo_of(p, B, L);
+      const int b0 = tr.nb * geo.cpt;
+      const int nchrom = min(geo.cpt, B - b0);
+      const int half = round_up(nchrom * p, 32) >> 1;
+      const int r = rank * half + rl;                  // column of B
+      const int nk = (n + BK - 1) / BK;
+      const int kb0 = k_begin(T, tr.m0);
+      const bool write = rl < half;
+      const bool valid = write && r < nchrom * p;    // columns in [nchrom*p, N) are zero
+      const int c = valid ? r / p : 0;
+      const uint32_t lpair = (0x4000u | (uint32_t)(valid ? r - c * p : 0)) * 0x00010001u;
+      const uint4* src = reinterpret_cast<const uint4*>(T.pop.slot + (long long)(b0 + c) * ns) + 2 * kh;
+      // slot codes of the next K block are loaded one block ahead
+      uint4 n0 = zero4, n1 = zero4;
+      if (valid) {
+        const uint4* f = src + kb0 * (BK / 16);
+        n0 = __ldg(f); n1 = __ldg(f + 1);
+      }
+      for (int kb = kb0; kb < nk; ++kb, ring.next()) {
+        const uint4 q0 = n0, q1 = n1;
+        if (valid && kb + 1 < nk) {
+          const uint4* nx = src + (kb + 1) * (BK / 16);
+          n0 = __ldg(nx); n1 = __ldg(nx + 1);
+        }
+        const int s = ring.s;
+        if (!(ok = wait_warp(bars.empty(s), ring.ph ^ 1u, abort_flag, status))) break;
+        const uint32_t dst = base + s * STAGE_BYTES + 2 * A_BYTES + (uint32_t)rl * 128u;
+        const uint32_t q = 4u * (uint32_t)kh;
+        if (valid) {
+          st_shared_v4(dst + (((q + 0u) ^ swz) << 4), onehot8_set(q0.x, q0.y, lpair));
+          st_shared_v4(dst + (((q + 1u) ^ swz) << 4), onehot8_set(q0.z, q0.w, lpair));
+          st_shared_v4(dst + (((q + 2u) ^ swz) << 4), onehot8_set(q1.x, q1.y, lpair));
+          st_shared_v4(dst + (((q + 3u) ^ swz) << 4), onehot8_set(q1.z, q1.w, lpair));
+        } else if (write) {
+#pragma unroll
+          for (uint32_t u = 0; u < 4; ++u) st_shared_v4(dst + (((q + u) ^ swz) << 4), zero4);
+        }
+        ptx::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          if (rank == 0 && warp == kProdWarp0)
+            ptx::mbar_arrive_expect_tx(bars.full_oh(s), 16);
+          else
+            ptx::mbar_arrive(bars.full_oh(s));
+        }
+      }
+    }
+  } else if (!kPair && warp >= kProdWarp0) {
     // -------------------------------------------------------- one-hot producers
     const int r = threadIdx.x - 32 * kProdWarp0;
     Ring ring(STAGES);
     bool ok = true;
-    for (int rd = 0, g = tile_of_round(0, snake); g < total_tiles && ok; g = tile_of_round(++rd, snake)) {
-      const TileRef tr = decode_tile(tp, g, L);
+    for (int rd = 0, g = tile_of_round(0, snake, 0); g < total_tiles && ok; g = tile_of_round(++rd, snake, 0)) {
+      const TileRef tr = decode_tile(tp, g, L, 0);
       const Task& T = task_at(tp, tr.task);
       const int n = T.in.n, p = T.in.p, ns = T.in.ns, B = T.pop.B;
       const Geo geo = geo_of(p, B, L);
@@ -676,16 +855,52 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   ptx::tc_fence_before();
   __syncthreads();
+  // in pair mode neither CTA frees its TMEM or exits while rank 0's MMAs may
+  // still use the other's shared memory and TMEM (rank 0 has drained them
+  // before it reaches this barrier)
+  if constexpr (kPair) ptx::cluster_sync();
   if (warp == 1) {
     ptx::tc_fence_after();
-    ptx::tmem_dealloc(tmem, tmem_cols);
+    if constexpr (kPair)
+      ptx::tmem_dealloc_pair(tmem, tmem_cols);
+    else
+      ptx::tmem_dealloc(tmem, tmem_cols);
   }
 }
 
 int tc_part_rows(int n) { return 4 * ((n + BM - 1) / BM); }
 
+// Clusters of two that can run at once on each device (pair mode's grid),
+// found once per device when its handles are set up.
+static int g_pair_slots[64];
+
 void prepare_eval_tc() {
-  cudaFuncSetAttribute(k_eval_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  cudaFuncSetAttribute(k_eval_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  cudaFuncSetAttribute(k_eval_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || g_pair_slots[dev] > 0) return;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = kSmemBytes;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, k_eval_tc<true>, &cfg) == cudaSuccess && clusters > 0)
+    g_pair_slots[dev] = clusters;
+  else
+    cudaGetLastError();
+}
+
+int tc_pair_slots() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  return g_pair_slots[dev];
 }
 
 bool tc_tile_fits(const TcTile& t, int p) { return lay_of(t).ok && p <= t.ntile; }
@@ -697,19 +912,28 @@ void launch_eval_tc(const TaskSet& ts, int num_sms, uint32_t* status, cudaStream
   TcTile t = tile;
   for (int k = 0; k < ts.count; ++k)
     if (!tc_tile_fits(t, ts.h[k].in.p)) t = TcTile{};
+  // pair mode needs its cluster slots counted (prepare_eval_tc)
+  const int slots = tc_pair_slots();
+  if (t.pair && slots <= 0) t.pair = 0;
   const Lay L = lay_of(t);
   TaskParam tp = make_param(ts);
   for (int k = 0; k < ts.count; ++k) {
     const Task& T = ts.h[k];
     const int mt = (T.in.n + BM - 1) / BM;
-    tp.bo.o[k + 1] = tp.bo.o[k] + (T.pop.B > 0 ? mt * geo_of(T.in.p, T.pop.B, L).nt : 0);
+    const int mu = L.pair ? (mt + 1) / 2 : mt;   // row units
+    tp.bo.o[k + 1] = tp.bo.o[k] + (T.pop.B > 0 ? mu * geo_of(T.in.p, T.pop.B, L).nt : 0);
   }
   const int total = tp.bo.o[ts.count];
   if (total == 0) return;
   int snake = 0;
   for (int k = 0; k < ts.count; ++k) snake |= ts.h[k].in.wtri;
-  const int grid = total < num_sms ? total : num_sms;
-  launch_pdl(k_eval_tc, grid, kThreads, kSmemBytes, s, tp, total, status, L, snake);
+  if (L.pair) {
+    const int pairs = total < slots ? total : slots;
+    launch_pdl_cluster(k_eval_tc<true>, 2 * pairs, kThreads, kSmemBytes, s, 2, tp, total, status, L, snake);
+  } else {
+    const int grid = total < num_sms ? total : num_sms;
+    launch_pdl(k_eval_tc<false>, grid, kThreads, kSmemBytes, s, tp, total, status, L, snake);
+  }
 }
 
 // Self-test of the bounded waits: the warps of one block wait on an mbarrier

@@ -27,6 +27,27 @@ inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
   cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
+// launch_pdl with clusters of `cluster` consecutive blocks (grid a multiple).
+template <class... KArgs, class... Args>
+inline void launch_pdl_cluster(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                               int cluster, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  attr[1].id = cudaLaunchAttributeClusterDimension;
+  attr[1].val.clusterDim.x = (unsigned)cluster;
+  attr[1].val.clusterDim.y = 1;
+  attr[1].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // Block ranges of the tasks of one launch: task t owns global blocks
 // [o[t], o[t+1]).  Passed by value so that a captured graph keeps it.
 struct BlockOffsets {
@@ -114,12 +135,15 @@ void prepare_eval_plain(int max_smem);
 // Tile shape of a launch: MMA width ntile (64, 128 or 256 columns; a tile
 // holds floor(ntile/p) chromosomes), shared-memory stages (2..4) and the
 // raster order of the persistent tile loop (0: column tiles of a row block
-// first, 1: row blocks of a column tile first).  The results do not depend
-// on it.
+// first, 1: row blocks of a column tile first) and the CTA-pair mode (1: a
+// cluster of two CTAs runs each M = 256 MMA over two row blocks, each CTA
+// holding its row block of U and half of the one-hot columns).  The results
+// do not depend on it.
 struct TcTile {
   int ntile = 256;
   int stages = 3;
   int raster = 0;
+  int pair = 0;
 };
 // true when the shape's layout fits shared memory and p <= ntile
 bool tc_tile_fits(const TcTile& t, int p);
@@ -127,6 +151,9 @@ size_t tc_slab_bytes(const TcTile& t);
 void launch_eval_tc(const TaskSet& ts, int num_sms, uint32_t* status, cudaStream_t s,
                     const TcTile& tile = TcTile{});
 int tc_part_rows(int n);
+// Clusters of two CTAs the pair-mode evaluator can run at once on the current
+// device (0 before prepare_eval_tc, or when none fits).
+int tc_pair_slots();
 // Runs k_wait_selftest (see eval_tc.cu); 0 or a USAPHMP_E* code.
 int selftest_wait_timeout(uint64_t limit_ns, uint32_t* status, unsigned long long* elapsed_ns);
 void prepare_eval_tc();

@@ -8,7 +8,7 @@
 //   {"format": "usaphmp-tile-cache-1",
 //    "entries": [
 //      {"device": "NVIDIA GB300", "n_blocks": 8, "p": 20, "B_pow2": 4096,
-//       "ntile": 256, "stages": 3, "raster": 0, "ms": 0.2091}, ...]}
+//       "ntile": 256, "stages": 3, "raster": 0, "pair": 0, "ms": 0.2091}, ...]}
 //
 // A bucket is (device name, ceil(n/128) row blocks, p, B rounded up to a
 // power of two): the tile count and the per-tile work of the kernel depend on
@@ -195,10 +195,13 @@ int read_cache(const char* path, std::vector<Entry>& out, std::string* why) {
         !num("ntile", &nt) || !num("stages", &st) || !num("raster", &ra))
       continue;  // an entry of another shape: skipped
     num("ms", &ms);
+    double pr = 0;
+    num("pair", &pr);   // absent in caches written before pair mode: 0
     Entry x;
     x.device = dev->str;
     x.n_blocks = (int)nb; x.p = (int)p; x.b_pow2 = (int)b;
     x.tile.ntile = (int32_t)nt; x.tile.stages = (int32_t)st; x.tile.raster = (int32_t)ra;
+    x.tile.pair = (int32_t)pr;
     x.ms = ms;
     out.push_back(x);
   }
@@ -212,9 +215,9 @@ int write_cache(const char* path, const std::vector<Entry>& ents, std::string* w
     char buf[512];
     std::snprintf(buf, sizeof(buf),
                   "%s\n  {\"device\": %s, \"n_blocks\": %d, \"p\": %d, \"B_pow2\": %d, \"ntile\": %d, "
-                  "\"stages\": %d, \"raster\": %d, \"ms\": %.6f}",
+                  "\"stages\": %d, \"raster\": %d, \"pair\": %d, \"ms\": %.6f}",
                   k ? "," : "", quote(e.device).c_str(), e.n_blocks, e.p, e.b_pow2, e.tile.ntile, e.tile.stages,
-                  e.tile.raster, e.ms);
+                  e.tile.raster, e.tile.pair, e.ms);
     text += buf;
   }
   text += "\n ]}\n";

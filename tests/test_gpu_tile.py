@@ -11,7 +11,12 @@ from paper_1704_06258_gb300.binding import PATH_PLAIN_FP32, PATH_SPLIT_BF16, Ins
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(nt, st, ra) for nt in (256, 128, 64) for st in (2, 3, 4) for ra in (0, 1) if not (nt == 256 and st == 4)]
+# (ntile, stages, raster, pair): one CTA per MMA (ntile 256: at most 3 stages),
+# or CTA pairs with M = 256 MMAs (half the one-hot operand per CTA: 4 stages fit)
+SHAPES = [(nt, st, ra, 0) for nt in (256, 128, 64) for st in (2, 3, 4) for ra in (0, 1) if not (nt == 256 and st == 4)]
+SHAPES += [(nt, st, ra, 1) for nt in (256, 128, 64) for st in (2, 3, 4) for ra in (0, 1)]
+KEYS = ("ntile", "stages", "raster", "pair")
+DEFAULT = {"ntile": 256, "stages": 3, "raster": 0, "pair": 0}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -25,29 +30,29 @@ def test_every_shape_gives_bit_identical_fitness(n, p, B):
     hubs, S = synth.random_population(n * 7 + p, n, p, B)
     with Instance.from_instance(inst) as gi:
         gi.set_params(path=PATH_SPLIT_BF16)
-        assert gi.get_tile() == {"ntile": 256, "stages": 3, "raster": 0}
+        assert gi.get_tile() == DEFAULT
         base = gi.eval(hubs, S)
-        for nt, st, ra in SHAPES:
-            if nt < p:
+        for shape in SHAPES:
+            if shape[0] < p:
                 with pytest.raises(UsaphmpError):
-                    gi.set_tile(nt, st, ra)
+                    gi.set_tile(*shape)
                 continue
-            gi.set_tile(nt, st, ra)
-            assert gi.get_tile() == {"ntile": nt, "stages": st, "raster": ra}
-            np.testing.assert_array_equal(gi.eval(hubs, S), base, err_msg=str((nt, st, ra)))
+            gi.set_tile(*shape)
+            assert gi.get_tile() == dict(zip(KEYS, shape))
+            np.testing.assert_array_equal(gi.eval(hubs, S), base, err_msg=str(shape))
     ref = np.array([cost.pair_cost(inst.W, inst.C, inst.chi, inst.alpha, inst.delta, s) for s in S[:8]])
     assert (np.abs(base[:8] - ref) / ref).max() <= 1e-4
 
 
 @pytest.mark.parametrize("shape", [(32, 3, 0), (512, 2, 0), (256, 4, 0), (128, 1, 0), (128, 5, 0), (128, 3, 2),
-                                   (64, 3, 0)])
+                                   (128, 3, 0, 2), (256, 5, 0, 1), (64, 3, 0)])
 def test_invalid_shapes_are_refused(shape):
     inst = synth.urand200(seed=3, n=120, p=100)
     with Instance.from_instance(inst) as gi:
         with pytest.raises(UsaphmpError) as e:
             gi.set_tile(*shape)           # the last one: ntile 64 < p = 100
         assert e.value.name == "EINVAL"
-        assert gi.get_tile() == {"ntile": 256, "stages": 3, "raster": 0}
+        assert gi.get_tile() == DEFAULT
 
 
 def test_autotune_picks_a_valid_shape_and_caches_it(tmp_path):
@@ -56,10 +61,10 @@ def test_autotune_picks_a_valid_shape_and_caches_it(tmp_path):
     with Instance.from_instance(inst) as gi:
         gi.set_params(islands=4, island_size=32, path=PATH_SPLIT_BF16)
         got = gi.autotune(reps=3, cache=cache)
-        assert (got["ntile"], got["stages"], got["raster"]) in SHAPES
+        assert tuple(got[k] for k in KEYS) in SHAPES
         assert not got["from_cache"]
         assert 0 < got["ms"] <= got["default_ms"]
-        assert gi.get_tile() == {k: got[k] for k in ("ntile", "stages", "raster")}
+        assert gi.get_tile() == {k: got[k] for k in KEYS}
         with pytest.raises(UsaphmpError):
             gi.ga_run(1)                   # the tuner reset the GA state
         entries = json.load(open(cache))["entries"]
@@ -70,7 +75,7 @@ def test_autotune_picks_a_valid_shape_and_caches_it(tmp_path):
         gi.set_params(islands=4, island_size=32, path=PATH_SPLIT_BF16)
         again = gi.autotune(reps=3, cache=cache)
         assert again["from_cache"] and again["ms"] == 0.0
-        assert {k: again[k] for k in ("ntile", "stages", "raster")} == {k: got[k] for k in ("ntile", "stages", "raster")}
+        assert {k: again[k] for k in KEYS} == {k: got[k] for k in KEYS}
         gi.set_tile(256, 3, 0)
         default = gi.solve(generations=12, seed=5)
     # the shape changes speed only

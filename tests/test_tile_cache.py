@@ -24,7 +24,7 @@ def test_store_then_lookup_by_bucket(tmp_path):
     binding.tile_cache_store(path, DEV, 6000, 50, 2048, 256, 2, 0, 7.5)
     # same bucket: ceil(n/128) row blocks, p, population rounded up to a power of two
     got = binding.tile_cache_lookup(path, DEV, 1024, 20, 2049)
-    assert got == {"ntile": 128, "stages": 3, "raster": 1, "ms": 0.25}
+    assert got == {"ntile": 128, "stages": 3, "raster": 1, "pair": 0, "ms": 0.25}
     assert binding.tile_cache_lookup(path, DEV, 5993, 50, 1100)["stages"] == 2
     # other buckets
     assert binding.tile_cache_lookup(path, DEV, 1025, 20, 4096) is None      # 9 row blocks
@@ -33,6 +33,14 @@ def test_store_then_lookup_by_bucket(tmp_path):
     assert binding.tile_cache_lookup(path, "NVIDIA B200", 1000, 20, 4096) is None
     doc = json.load(open(path))
     assert doc["format"] == "usaphmp-tile-cache-1" and len(doc["entries"]) == 2
+
+
+def test_pair_mode_round_trips(tmp_path):
+    path = str(tmp_path / "c.json")
+    binding.tile_cache_store(path, DEV, 6000, 20, 2048, 256, 4, 1, 1.5, pair=1)
+    assert json.load(open(path))["entries"][0]["pair"] == 1
+    assert binding.tile_cache_lookup(path, DEV, 6000, 20, 2048) == {"ntile": 256, "stages": 4, "raster": 1,
+                                                                   "pair": 1, "ms": 1.5}
 
 
 def test_store_replaces_the_bucket_entry(tmp_path):
@@ -62,7 +70,8 @@ def test_hand_written_file_with_extra_keys_and_foreign_entries(tmp_path):
     with open(path, "w") as f:
         json.dump(doc, f, indent=3)
     got = binding.tile_cache_lookup(path, DEV, 1000, 20, 4096)
-    assert got == {"ntile": 64, "stages": 2, "raster": 1, "ms": 0.0}
+    # written before pair mode: no "pair" key, read as 0
+    assert got == {"ntile": 64, "stages": 2, "raster": 1, "pair": 0, "ms": 0.0}
 
 
 @pytest.mark.parametrize("text", ['{"format": "usaphmp-tile-cache-1", "entries": [',
