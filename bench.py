@@ -40,11 +40,11 @@ CSRC = os.path.join(ROOT, "paper_1704_06258_gb300", "csrc")
 # to it (null otherwise: the kernel changed since the capture).
 PROFILED = {
     "k_eval_tc": {"files": ["eval_tc.cu", "tc_ptx.cuh", "common.cuh"],
-                  "sha256": "695765be206f5131c9431ea904496069a45c65b60a3852fa93b6f0d277288c92",
-                  "dram_bytes": 13384000, "tensor_pipe_active": 0.587},
+                  "sha256": "a0116f664be45734f0a786db52d2e1cbf5139f4cd9bb59c1ca781c63870fce3f",
+                  "dram_bytes": 13726000, "tensor_pipe_active": 0.616},
     "k_alloc": {"files": ["alloc.cu", "common.cuh"],
-                "sha256": "7792a84cf0a3c539771432ad18d9883b01b8310aeb697e8133451822582ec34c",
-                "dram_bytes": 4359000, "alu_pipe_active": 0.577},
+                "sha256": "8985f1e9de9f08f60aad864c8a5c966e15d66e425da51b4e4d155a02469b5e8f",
+                "dram_bytes": 4359000, "alu_pipe_active": 0.578},
 }
 # ALU lanes per SM (4 sub-partitions x 16 lanes of the integer / compare /
 # select pipe): the peak of the nearest-hub search, which is compares and
