@@ -256,6 +256,16 @@ __global__ void __launch_bounds__(kAllocThreads) k_alloc(const __grid_constant__
 #define USAPHMP_ALLOC_WARPS 4
 #endif
 constexpr int kAllocWarps = USAPHMP_ALLOC_WARPS;   // warps per block
+// Four-node groups a thread searches at once (their loads in flight together).
+constexpr int kAllocGroups = 2;
+// Four-node groups a thread gathers at once when the slots are given.
+constexpr int kGivenGroups = 3;
+// Row offsets of hubs 1, 5, 9, ... start on 16-byte boundaries: entry k at
+// kHoPad + k of a row of kHoRow ints (a multiple of four, so every warp's
+// row starts on a 16-byte boundary too).
+constexpr int kHoPad = 3;
+constexpr int kHoRow = (kHoPad + kMaxP + 1 + 3) / 4 * 4;
+static_assert(kHoRow % 4 == 0 && kHoRow >= kHoPad + kMaxP, "hub offset rows");
 
 __host__ __device__ inline int alloc_warps_per_chrom(int n) { return n <= 2048 ? 1 : (n <= 4096 ? 2 : 4); }
 
@@ -264,6 +274,7 @@ __host__ __device__ inline int alloc_warps_per_chrom(int n) { return n <= 2048 ?
 template <bool kNearest>
 __global__ void __launch_bounds__(32 * kAllocWarps) k_alloc_warp(const __grid_constant__ TaskParam tp, int with_chub) {
   __shared__ int hs_all[kAllocWarps][kMaxP];
+  __shared__ __align__(16) int ho_all[kAllocWarps][kHoRow];
   __shared__ float red[kAllocWarps];
   pdl_wait();
   pdl_allow_next();
@@ -283,6 +294,7 @@ __global__ void __launch_bounds__(32 * kAllocWarps) k_alloc_warp(const __grid_co
   const float chi = T.in.chi, delta = T.in.delta;
   const bool sym = T.in.symmetric != 0;
   int* hs = hs_all[wib - wl];                      // the chromosome's first warp's row
+  int* ho = ho_all[wib - wl];                      // ho[kHoPad + k] = float4 offset of CT row hs[k]
   const int u0 = wl * 32 + lane, stride = 32 * G;  // thread within the chromosome
   bool bad = false;
   float acc = 0.f;
@@ -293,6 +305,7 @@ __global__ void __launch_bounds__(32 * kAllocWarps) k_alloc_warp(const __grid_co
       int v = T.pop.hubs_in ? T.pop.hubs_in[(long long)b * p + k] : T.pop.hubs[(long long)b * p + k];
       if (v < 0 || v >= n) { bad = true; v = 0; }
       hs[k] = v;
+      ho[kHoPad + k] = v * (ldw >> 2);
       if (T.pop.hubs_in) T.pop.hubs[(long long)b * p + k] = v;
     }
   }
@@ -302,92 +315,141 @@ __global__ void __launch_bounds__(32 * kAllocWarps) k_alloc_warp(const __grid_co
     const uint8_t* __restrict__ slot_in = T.pop.slot_in ? T.pop.slot_in + (long long)b * ns : slot;
     const int n4 = (n + 3) >> 2;
     if (kNearest) {
+      // kAllocGroups of the thread's groups at a time (more loads in flight);
+      // the hub rows' float4 offsets come four at a time from shared memory
+      const float4* __restrict__ CT4 = reinterpret_cast<const float4*>(CT);
       int kp = 0;   // first hub not below the current group's first node
-      for (int g = u0; g < n4; g += stride) {
-        const int i0 = g << 2;
-        float4 best = __ldg(reinterpret_cast<const float4*>(CT + (long long)hs[0] * ldw) + g);
-        int s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+      for (int g = u0; g < n4; g += kAllocGroups * stride) {
+        float4 best[kAllocGroups];
+        int sl[kAllocGroups][4];
+        const float4* col[kAllocGroups];   // column group gj of CT (a valid one for a missing group)
+#pragma unroll
+        for (int j = 0; j < kAllocGroups; ++j) {
+          const int gj = g + j * stride;
+          col[j] = CT4 + (gj < n4 ? gj : g);
+          best[j] = __ldg(col[j] + ho[kHoPad]);
+          sl[j][0] = sl[j][1] = sl[j][2] = sl[j][3] = 0;
+        }
         int l = 1;
         for (; l + 4 <= p; l += 4) {
-          float4 v[4];
+          const int4 o = *reinterpret_cast<const int4*>(ho + kHoPad + l);
+          const int off[4] = {o.x, o.y, o.z, o.w};
+          float4 v[kAllocGroups][4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) v[u] = __ldg(reinterpret_cast<const float4*>(CT + (long long)hs[l + u] * ldw) + g);
+          for (int u = 0; u < 4; ++u)
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            if (v[u].x < best.x) { best.x = v[u].x; s0 = l + u; }
-            if (v[u].y < best.y) { best.y = v[u].y; s1 = l + u; }
-            if (v[u].z < best.z) { best.z = v[u].z; s2 = l + u; }
-            if (v[u].w < best.w) { best.w = v[u].w; s3 = l + u; }
-          }
+            for (int j = 0; j < kAllocGroups; ++j) v[j][u] = __ldg(col[j] + off[u]);
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int j = 0; j < kAllocGroups; ++j) {
+              if (v[j][u].x < best[j].x) { best[j].x = v[j][u].x; sl[j][0] = l + u; }
+              if (v[j][u].y < best[j].y) { best[j].y = v[j][u].y; sl[j][1] = l + u; }
+              if (v[j][u].z < best[j].z) { best[j].z = v[j][u].z; sl[j][2] = l + u; }
+              if (v[j][u].w < best[j].w) { best[j].w = v[j][u].w; sl[j][3] = l + u; }
+            }
         }
         for (; l < p; ++l) {
-          const float4 v = __ldg(reinterpret_cast<const float4*>(CT + (long long)hs[l] * ldw) + g);
-          if (v.x < best.x) { best.x = v.x; s0 = l; }
-          if (v.y < best.y) { best.y = v.y; s1 = l; }
-          if (v.z < best.z) { best.z = v.z; s2 = l; }
-          if (v.w < best.w) { best.w = v.w; s3 = l; }
-        }
-        // hubs inside the group serve themselves
-        while (kp < p && hs[kp] < i0) ++kp;
-        for (int k = kp; k < p && hs[k] < i0 + 4; ++k) {
-          const int h = hs[k];
-          const float own = CT[(long long)h * ldw + h];
-          switch (h - i0) {
-            case 0: s0 = k; best.x = own; break;
-            case 1: s1 = k; best.y = own; break;
-            case 2: s2 = k; best.z = own; break;
-            default: s3 = k; best.w = own; break;
+          const int off = ho[kHoPad + l];
+#pragma unroll
+          for (int j = 0; j < kAllocGroups; ++j) {
+            const float4 v = __ldg(col[j] + off);
+            if (v.x < best[j].x) { best[j].x = v.x; sl[j][0] = l; }
+            if (v.y < best[j].y) { best[j].y = v.y; sl[j][1] = l; }
+            if (v.z < best[j].z) { best[j].z = v.z; sl[j][2] = l; }
+            if (v.w < best[j].w) { best[j].w = v.w; sl[j][3] = l; }
           }
         }
-        const float4 o4 = __ldg(reinterpret_cast<const float4*>(O) + g);
-        const float4 d4 = __ldg(reinterpret_cast<const float4*>(D) + g);
-        // one node of the group: access terms (in node order) and slot code
-        auto node = [&](int k, int sk, float cih, float oi, float di) -> uint32_t {
-          const int i = i0 + k;
-          if (i >= n) return (uint32_t)kSlotPad << (8 * k);
-          const float chi_i = sym ? cih : C[(long long)hs[sk] * ldw + i];   // C[h(i), i]
-          acc += access_term(chi, oi, cih, delta, di, chi_i);
-          return (uint32_t)sk << (8 * k);
-        };
-        uint32_t packed = node(0, s0, best.x, o4.x, d4.x);
-        packed |= node(1, s1, best.y, o4.y, d4.y);
-        packed |= node(2, s2, best.z, o4.z, d4.z);
-        packed |= node(3, s3, best.w, o4.w, d4.w);
-        *reinterpret_cast<uint32_t*>(slot + i0) = packed;
+#pragma unroll
+        for (int j = 0; j < kAllocGroups; ++j) {
+          const int gj = g + j * stride;
+          if (gj >= n4) break;
+          const int i0 = gj << 2;
+          // hubs inside the group serve themselves
+          while (kp < p && hs[kp] < i0) ++kp;
+          for (int q = kp; q < p && hs[q] < i0 + 4; ++q) {
+            const int h = hs[q];
+            const float own = CT[(long long)h * ldw + h];
+            switch (h - i0) {
+              case 0: sl[j][0] = q; best[j].x = own; break;
+              case 1: sl[j][1] = q; best[j].y = own; break;
+              case 2: sl[j][2] = q; best[j].z = own; break;
+              default: sl[j][3] = q; best[j].w = own; break;
+            }
+          }
+          const float4 o4 = __ldg(reinterpret_cast<const float4*>(O) + gj);
+          const float4 d4 = __ldg(reinterpret_cast<const float4*>(D) + gj);
+          // one node of the group: access terms (in node order) and slot code
+          auto node = [&](int k, int sk, float cih, float oi, float di) -> uint32_t {
+            const int i = i0 + k;
+            if (i >= n) return (uint32_t)kSlotPad << (8 * k);
+            const float chi_i = sym ? cih : C[(long long)hs[sk] * ldw + i];   // C[h(i), i]
+            acc += access_term(chi, oi, cih, delta, di, chi_i);
+            return (uint32_t)sk << (8 * k);
+          };
+          uint32_t packed = node(0, sl[j][0], best[j].x, o4.x, d4.x);
+          packed |= node(1, sl[j][1], best[j].y, o4.y, d4.y);
+          packed |= node(2, sl[j][2], best[j].z, o4.z, d4.z);
+          packed |= node(3, sl[j][3], best[j].w, o4.w, d4.w);
+          *reinterpret_cast<uint32_t*>(slot + i0) = packed;
+        }
       }
     } else {
-      for (int g = u0; g < n4; g += stride) {
-        const int i0 = g << 2;
-        const uint32_t codes = *reinterpret_cast<const uint32_t*>(slot_in + i0);
-        int bl[4];
-        float cih[4], chi_i[4];
+      // given slots: kGivenGroups of the thread's groups at a time, their
+      // slot codes loaded together and then their gathers, so one group's
+      // loads do not wait for the previous group's
+      for (int g = u0; g < n4; g += kGivenGroups * stride) {
+        uint32_t codes[kGivenGroups];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          bl[k] = (int)((codes >> (8 * k)) & 0xFFu);
-          if (i0 + k < n && bl[k] >= p) bad = true;
-          if (i0 + k >= n || bl[k] >= p) bl[k] = 0;
+        for (int j = 0; j < kGivenGroups; ++j) {
+          const int gj = g + j * stride;
+          codes[j] = gj < n4 ? *reinterpret_cast<const uint32_t*>(slot_in + (gj << 2)) : 0u;
         }
+        int bl[kGivenGroups][4];
+        float cih[kGivenGroups][4], chi_i[kGivenGroups][4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int i = min(i0 + k, n - 1);
-          cih[k] = CT[(long long)hs[bl[k]] * ldw + i];                       // C[i, h(i)]
-          chi_i[k] = sym ? cih[k] : C[(long long)hs[bl[k]] * ldw + i];      // C[h(i), i]
-        }
-        const float4 o4 = __ldg(reinterpret_cast<const float4*>(O) + g);
-        const float4 d4 = __ldg(reinterpret_cast<const float4*>(D) + g);
-        const float ok[4] = {o4.x, o4.y, o4.z, o4.w}, dk[4] = {d4.x, d4.y, d4.z, d4.w};
-        uint32_t packed = 0u;
+        for (int j = 0; j < kGivenGroups; ++j) {
+          const int gj = g + j * stride;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int i = i0 + k;
-          if (i < n) {
-            acc += access_term(chi, ok[k], cih[k], delta, dk[k], chi_i[k]);
-            packed |= (uint32_t)bl[k] << (8 * k);
-          } else {
-            packed |= (uint32_t)kSlotPad << (8 * k);
+          for (int k = 0; k < 4; ++k) {
+            const int i = (gj << 2) + k;
+            const bool valid = gj < n4 && i < n;
+            bl[j][k] = (int)((codes[j] >> (8 * k)) & 0xFFu);
+            if (valid && bl[j][k] >= p) bad = true;
+            if (!valid || bl[j][k] >= p) bl[j][k] = 0;
           }
         }
-        *reinterpret_cast<uint32_t*>(slot + i0) = packed;
+#pragma unroll
+        for (int j = 0; j < kGivenGroups; ++j) {
+          const int gj = g + j * stride;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int e = ho[kHoPad + bl[j][k]] * 4 + min((gj << 2) + k, n - 1);   // hub row, node i
+            cih[j][k] = CT[e];                       // C[i, h(i)]
+            chi_i[j][k] = sym ? cih[j][k] : C[e];    // C[h(i), i]
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < kGivenGroups; ++j) {
+          const int gj = g + j * stride;
+          if (gj >= n4) break;
+          const int i0 = gj << 2;
+          const float4 o4 = __ldg(reinterpret_cast<const float4*>(O) + gj);
+          const float4 d4 = __ldg(reinterpret_cast<const float4*>(D) + gj);
+          const float ok[4] = {o4.x, o4.y, o4.z, o4.w}, dk[4] = {d4.x, d4.y, d4.z, d4.w};
+          uint32_t packed = 0u;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int i = i0 + k;
+            if (i < n) {
+              acc += access_term(chi, ok[k], cih[j][k], delta, dk[k], chi_i[j][k]);
+              packed |= (uint32_t)bl[j][k] << (8 * k);
+            } else {
+              packed |= (uint32_t)kSlotPad << (8 * k);
+            }
+          }
+          *reinterpret_cast<uint32_t*>(slot + i0) = packed;
+        }
       }
     }
     for (int i = (n4 << 2) + u0; i < ns; i += stride) slot[i] = kSlotPad;
@@ -404,12 +466,18 @@ __global__ void __launch_bounds__(32 * kAllocWarps) k_alloc_warp(const __grid_co
   }
   if (live && wl == 0 && lane == 0) T.pop.t12[b] = acc;
   if (live && (with_chub || plain_global_table(p, ns))) {
+    // lane l of each warp takes column l of 32-column chunks, the
+    // chromosome's G warps rows k = wl, wl + G, ...: the column's hub is read
+    // once and the rows' gathers are independent of each other
     const int hst = chub_hstride(p), cst = chub_cstride(p);
     float* ch = T.pop.chub + (long long)b * cst;
-    for (int e = u0; e < cst; e += stride) {
-      const int k = e / hst, l = e - k * hst;
-      ch[e] = (k < p && l < p) ? C[(long long)hs[k] * ldw + hs[l]] : 0.f;
+    for (int l = lane; l < hst; l += 32) {
+      const int hl = l < p ? hs[l] : -1;
+#pragma unroll 4
+      for (int k = wl; k < p; k += G)
+        ch[k * hst + l] = hl >= 0 ? C[(long long)hs[k] * ldw + hl] : 0.f;
     }
+    for (int e = p * hst + u0; e < cst; e += stride) ch[e] = 0.f;
   }
 }
 

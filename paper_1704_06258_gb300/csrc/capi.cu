@@ -476,12 +476,12 @@ void drop_graph(usaphmp_s* h) {
   h->graph = nullptr;
 }
 
-// Chunks of a host-buffer evaluation: about 2048 chromosomes each, one for
-// smaller calls.  The copy of a later chunk overlaps the evaluation of an
-// earlier one; smaller chunks lose more to their own launches and to
-// tensor-core tiles left idle at the end of each chunk than they gain.
+// Chunks of a host-buffer evaluation: about 1024 chromosomes each (at most
+// 8), one for smaller calls.  The canonical form and the access terms of a
+// chunk run while the later chunks are still being copied; the transfer term
+// then runs once over all B (one launch keeps the tensor-core tiles full).
 #ifndef USAPHMP_EVAL_CHUNK
-#define USAPHMP_EVAL_CHUNK 2048
+#define USAPHMP_EVAL_CHUNK 1024
 #endif
 int eval_chunks(int B) {
   const int K = B / USAPHMP_EVAL_CHUNK;
@@ -836,12 +836,12 @@ int usaphmp_eval(usaphmp_t h, int32_t B, const int32_t* hubs, const int32_t* S, 
     CK(cudaMallocHost(&h->h_fit_out, sizeof(float) * B));
     h->in_cap = B;
   }
-  // The inputs arrive in K chunks on a copy stream; each chunk is evaluated
-  // whole (canonical form, access terms, transfer term, reduction, fitness
-  // copy-out) as soon as it has landed, so the copies of the later chunks
-  // overlap the evaluation of the earlier ones.  A chromosome's fitness does
-  // not depend on the chunk it is evaluated in (every stage works per
-  // chromosome and sums in a fixed order).
+  // The inputs arrive in K chunks on a copy stream; the canonical form and
+  // the allocation kernel (access terms, hub-cost tables) of each chunk run
+  // as soon as it has landed, overlapping the copies of the later chunks,
+  // and the transfer term and the reduction then run once over all B.  A
+  // chromosome's fitness does not depend on the chunk or the batch it is
+  // evaluated in (every stage works per chromosome and sums in a fixed order).
   const int K = eval_chunks(B);
   if (K > 1 && !h->copy_stream) {
     CK(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
@@ -855,12 +855,7 @@ int usaphmp_eval(usaphmp_t h, int32_t B, const int32_t* hubs, const int32_t* S, 
     cudaStreamSynchronize(s);
     return rc;
   };
-  size_t part_need = 0;
-  for (int k = 0; k < K; ++k) {
-    const int nb = (int)((long long)B * (k + 1) / K) - (int)((long long)B * k / K);
-    part_need += (size_t)part_rows(h, nb) * nb;
-  }
-  int rc = ensure_pop(h, h->ev, B, part_need);
+  int rc = ensure_pop(h, h->ev, B);
   if (rc != USAPHMP_OK) return rc;
   if (use_fp64(h) && (rc = ensure_fp64(h, B)) != USAPHMP_OK) return rc;
   if ((rc = reset_status(h, s)) != USAPHMP_OK) return finish(rc);
@@ -868,7 +863,6 @@ int usaphmp_eval(usaphmp_t h, int32_t B, const int32_t* hubs, const int32_t* S, 
   full.fit = h->d_fit_out;
   full.out_scale = (float)output_scale(h);
   const int cst = chub_cstride(h->p);
-  size_t part_off = 0;
   for (int k = 0; k < K; ++k) {
     const int c0 = (int)((long long)B * k / K), c1 = (int)((long long)B * (k + 1) / K), nb = c1 - c0;
     cudaError_t e = cudaMemcpyAsync(h->d_hubs_in + (size_t)c0 * h->p, hubs + (size_t)c0 * h->p,
@@ -887,14 +881,14 @@ int usaphmp_eval(usaphmp_t h, int32_t B, const int32_t* hubs, const int32_t* S, 
     pc.slot += (size_t)c0 * h->ns;
     pc.t12 += c0;
     pc.chub += (size_t)c0 * cst;
-    pc.fit += c0;
-    pc.part += part_off;
-    pc.npart = part_rows(h, nb);
-    part_off += (size_t)pc.npart * nb;
-    if ((rc = run_eval(h, make_task(h, pc), false, s)) != USAPHMP_OK) return finish(rc);
-    e = cudaMemcpyAsync(h->h_fit_out + c0, h->d_fit_out + c0, sizeof(float) * nb, cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return finish(cuda_fail(e, "usaphmp_eval fitness copy"));
+    const Task tc = make_task(h, pc);
+    TaskSet ts{nullptr, &tc, 1};
+    launch_alloc(ts, false, use_tc(h), s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return finish(cuda_fail(e, "usaphmp_eval allocation"));
   }
+  if ((rc = run_transfer(h, make_task(h, full), s)) != USAPHMP_OK) return finish(rc);
+  cudaError_t e = cudaMemcpyAsync(h->h_fit_out, h->d_fit_out, sizeof(float) * B, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return finish(cuda_fail(e, "usaphmp_eval fitness copy"));
   if ((rc = check_status(h, s, "usaphmp_eval")) != USAPHMP_OK) return rc;   // one synchronisation
   for (int b = 0; b < B; ++b) fitness[b] = h->h_fit_out[b];
   return USAPHMP_OK;
