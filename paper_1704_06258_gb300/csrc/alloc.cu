@@ -242,6 +242,34 @@ __global__ void __launch_bounds__(kAllocThreads) k_alloc(const __grid_constant__
   }
 }
 
+
+// Hub-cost table of one chromosome (layout in common.cuh): ch[k * hst + l] =
+// C[hs[k]][hs[l]] for k, l < p and 0 in the rest of its cst entries.  Thread
+// t of nt takes entries t, t + nt, ..., kBatch at a time with their loads
+// issued together; k = e / hst comes from a float product with the
+// reciprocal, corrected by one step either way (e < 2^16, so the product is
+// off by far less than one).
+template <int kBatch>
+__device__ inline void fill_chub(float* __restrict__ ch, const float* __restrict__ C, const int* hs, int p, int ldw,
+                                 int t, int nt) {
+  const int hst = chub_hstride(p), cst = chub_cstride(p);
+  const float inv = 1.0f / (float)hst;
+  for (int e0 = t; e0 < cst; e0 += kBatch * nt) {
+    float v[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int e = e0 + u * nt;
+      int k = (int)(((float)e + 0.5f) * inv);
+      int l = e - k * hst;
+      if (l < 0) { --k; l += hst; } else if (l >= hst) { ++k; l -= hst; }
+      v[u] = (e < cst && k < p && l < p) ? C[(long long)hs[k] * ldw + hs[l]] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u)
+      if (e0 + u * nt < cst) ch[e0 + u * nt] = v[u];
+  }
+}
+
 // Direct hub arcs: G warps per chromosome (G = 1, 2 or 4 by n alone), four
 // chromosomes' worth of warps per block.  Thread u of a chromosome's 32G
 // takes the four-node groups u, u + 32G, ...: one 16-byte load of
@@ -465,20 +493,171 @@ __global__ void __launch_bounds__(32 * kAllocWarps) k_alloc_warp(const __grid_co
     }
   }
   if (live && wl == 0 && lane == 0) T.pop.t12[b] = acc;
-  if (live && (with_chub || plain_global_table(p, ns))) {
-    // lane l of each warp takes column l of 32-column chunks, the
-    // chromosome's G warps rows k = wl, wl + G, ...: the column's hub is read
-    // once and the rows' gathers are independent of each other
-    const int hst = chub_hstride(p), cst = chub_cstride(p);
-    float* ch = T.pop.chub + (long long)b * cst;
-    for (int l = lane; l < hst; l += 32) {
-      const int hl = l < p ? hs[l] : -1;
-#pragma unroll 4
-      for (int k = wl; k < p; k += G)
-        ch[k * hst + l] = hl >= 0 ? C[(long long)hs[k] * ldw + hl] : 0.f;
-    }
-    for (int e = p * hst + u0; e < cst; e += stride) ch[e] = 0.f;
+  if (live && (with_chub || plain_global_table(p, ns)))
+    fill_chub<4>(T.pop.chub + (long long)b * chub_cstride(p), C, hs, p, ldw, u0, stride);
+}
+
+// Chromosomes given in the encoding of §4.1 (p hub node ids in any order and
+// S[i] = the hub serving node i), direct hub arcs: the validation and
+// canonical form (hubs ascending, slot codes = ranks of S[i] among them; the
+// checks of eq. 2, 3 and 5 and "a hub serves itself", §4.1) fused with the
+// given-slot allocation kernel above, whose groups, warps per chromosome and
+// summation order it keeps (the same t12 bits for the same slots).  S of a
+// thread's first kCanonGroups groups is loaded before the hub phase, so that
+// those loads overlap the hub loads and ranks.
+constexpr int kCanonGroups = 4;
+
+__global__ void __launch_bounds__(32 * kAllocWarps)
+k_canon_alloc(const __grid_constant__ Task T, const int32_t* __restrict__ hubs_in, const int32_t* __restrict__ S,
+              int* bad_index, int index_base, int with_chub) {
+  extern __shared__ __align__(16) unsigned char rank_all[];   // per chromosome: rank[n], 0xFF = not a hub
+  __shared__ int hs_all[kAllocWarps][kMaxP];
+  __shared__ __align__(16) int ho_all[kAllocWarps][kHoRow];
+  __shared__ int hraw_all[kAllocWarps][kMaxP];
+  __shared__ float red[kAllocWarps];
+  __shared__ int cbad[kAllocWarps];
+  pdl_wait();
+  pdl_allow_next();
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int n = T.in.n, p = T.in.p, ldw = T.in.ldw, ns = T.in.ns;
+  const int G = alloc_warps_per_chrom(n), cpb = kAllocWarps / G, wl = wib % G, c = wib / G;
+  const int b = blockIdx.x * cpb + c;
+  const bool live = b < T.pop.B;
+  const int n16 = round_up(n, 16), n4 = (n + 3) >> 2;
+  uint8_t* rank = rank_all + (size_t)c * n16;
+  int* hs = hs_all[wib - wl];
+  int* ho = ho_all[wib - wl];
+  int* hraw = hraw_all[wib - wl];
+  const int u0 = wl * 32 + lane, stride = 32 * G;
+  const float* __restrict__ C = T.in.C;
+  const float* __restrict__ CT = T.in.CT;
+  const float chi = T.in.chi, delta = T.in.delta;
+  const bool sym = T.in.symmetric != 0;
+  const int32_t* Sb = S + (long long)b * n;
+  int sv[kCanonGroups][4];
+  auto load_groups = [&](int g0) {
+#pragma unroll
+    for (int j = 0; j < kCanonGroups; ++j)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int i = ((g0 + j * stride) << 2) + k;
+        sv[j][k] = (live && g0 + j * stride < n4 && i < n) ? Sb[i] : 0;
+      }
+  };
+  if (threadIdx.x < kAllocWarps) cbad[threadIdx.x] = 0;
+  if (live) {
+    for (int q = u0; q < n16 / 16; q += stride) reinterpret_cast<uint4*>(rank)[q] = make_uint4(~0u, ~0u, ~0u, ~0u);
+    for (int k = u0; k < p; k += stride) hraw[k] = hubs_in[(long long)b * p + k];
   }
+  load_groups(u0);
+  __syncthreads();
+  bool bad = false;
+  if (live) {
+    for (int k = u0; k < p; k += stride) {
+      const int v = hraw[k];
+      if (v < 0 || v >= n) { bad = true; continue; }
+      int r = 0;
+      bool dup = false;
+      for (int l = 0; l < p; ++l) {
+        const int u = hraw[l];
+        r += u < v;
+        dup |= (u == v) & (l != k);
+      }
+      if (dup) { bad = true; continue; }
+      rank[v] = (uint8_t)r;
+      hs[r] = v;
+      ho[kHoPad + r] = v * (ldw >> 2);
+      T.pop.hubs[(long long)b * p + r] = v;
+    }
+    if (bad) cbad[c] = 1;
+  }
+  __syncthreads();
+  const bool ok = live && cbad[c] == 0;
+  float acc = 0.f;
+  if (ok) {
+    uint8_t* __restrict__ slot = T.pop.slot + (long long)b * ns;
+    for (int g0 = u0; g0 < n4; g0 += kCanonGroups * stride) {
+      if (g0 != u0) load_groups(g0);
+      // slot codes of the thread's groups (four per word), then all their gathers
+      uint32_t codes[kCanonGroups];
+#pragma unroll
+      for (int j = 0; j < kCanonGroups; ++j) {
+        codes[j] = 0u;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int i = ((g0 + j * stride) << 2) + k, s = sv[j][k];
+          uint32_t code = 0u;
+          if (g0 + j * stride < n4 && i < n) {
+            if (s < 0 || s >= n || rank[s] == kSlotPad || (rank[i] != kSlotPad && s != i))
+              bad = true;
+            else
+              code = rank[s];
+          }
+          codes[j] |= code << (8 * k);
+        }
+      }
+      float cih[kCanonGroups][4];
+#pragma unroll
+      for (int j = 0; j < kCanonGroups; ++j)
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          cih[j][k] = CT[ho[kHoPad + ((codes[j] >> (8 * k)) & 0xFFu)] * 4 +
+                         min(((g0 + j * stride) << 2) + k, n - 1)];   // C[i, h(i)]
+#pragma unroll
+      for (int j = 0; j < kCanonGroups; ++j) {
+        const int gj = g0 + j * stride;
+        if (gj >= n4) break;
+        const int i0 = gj << 2;
+        const float4 o4 = __ldg(reinterpret_cast<const float4*>(T.in.O) + gj);
+        const float4 d4 = __ldg(reinterpret_cast<const float4*>(T.in.D) + gj);
+        const float ok4[4] = {o4.x, o4.y, o4.z, o4.w}, dk[4] = {d4.x, d4.y, d4.z, d4.w};
+        uint32_t packed = 0u;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int i = i0 + k;
+          const uint32_t code = (codes[j] >> (8 * k)) & 0xFFu;
+          if (i < n) {
+            const float chi_i = sym ? cih[j][k] : C[ho[kHoPad + code] * 4 + i];   // C[h(i), i]
+            acc += access_term(chi, ok4[k], cih[j][k], delta, dk[k], chi_i);
+            packed |= code << (8 * k);
+          } else {
+            packed |= (uint32_t)kSlotPad << (8 * k);
+          }
+        }
+        *reinterpret_cast<uint32_t*>(slot + i0) = packed;
+      }
+    }
+    for (int i = (n4 << 2) + u0; i < ns; i += stride) slot[i] = kSlotPad;
+    if (bad) cbad[c] = 1;
+  }
+  acc = warp_sum(acc);
+  if (G > 1) {
+    if (lane == 0) red[wib] = acc;
+    __syncthreads();
+    if (wl == 0) {
+      acc = red[wib];
+      for (int w = 1; w < G; ++w) acc += red[wib + w];
+    }
+  }
+  if (ok && wl == 0 && lane == 0) T.pop.t12[b] = acc;
+  if (ok && (with_chub || plain_global_table(p, ns)))
+    fill_chub<8>(T.pop.chub + (long long)b * chub_cstride(p), C, hs, p, ldw, u0, stride);
+  __syncthreads();
+  if (live && wl == 0 && lane == 0 && cbad[c]) {
+    atomicOr(T.pop.status, kStatusBadChromosome);
+    atomicMin(bad_index, index_base + b);
+  }
+}
+
+bool launch_canon_alloc(const Task& task, const int32_t* hubs_in, const int32_t* S, int* bad_index, int index_base,
+                        bool with_chub, cudaStream_t s) {
+  if (task.in.routing != 0) return false;   // hub-path tables come from the block kernel
+  if (task.pop.B <= 0) return true;
+  const int cpb = kAllocWarps / alloc_warps_per_chrom(task.in.n);
+  const size_t smem = (size_t)cpb * round_up(task.in.n, 16);
+  launch_pdl(k_canon_alloc, (task.pop.B + cpb - 1) / cpb, 32 * kAllocWarps, smem, s, task, hubs_in, S, bad_index,
+             index_base, with_chub ? 1 : 0);
+  return true;
 }
 
 void launch_alloc(const TaskSet& ts, bool nearest, bool with_chub, cudaStream_t s) {

@@ -494,12 +494,16 @@ int enqueue_eval_canonical(usaphmp_s* h, int B, const int32_t* hubs_in, const in
                            cudaStream_t s) {
   RET(ensure_pop(h, h->ev, B));
   RET(reset_status(h, s));
-  launch_canon(hubs_in, S, B, h->n, h->p, h->ns, h->ev.hubs, h->ev.slot, h->d_status, h->d_bad, s);
-  CK(cudaGetLastError());
   PopBuf pb = popbuf(h, h->ev, B);
   pb.fit = fit_out;
   pb.out_scale = (float)output_scale(h);
   const Task task = make_task(h, pb);
+  if (launch_canon_alloc(task, hubs_in, S, h->d_bad, 0, use_tc(h), s)) {
+    CK(cudaGetLastError());
+    return run_transfer(h, task, s);
+  }
+  launch_canon(hubs_in, S, B, h->n, h->p, h->ns, h->ev.hubs, h->ev.slot, h->d_status, h->d_bad, s);
+  CK(cudaGetLastError());
   return run_eval(h, task, false, s);
 }
 
@@ -873,8 +877,6 @@ int usaphmp_eval(usaphmp_t h, int32_t B, const int32_t* hubs, const int32_t* S, 
     if (e == cudaSuccess && K > 1) e = cudaEventRecord(h->chunk_ev[k], cs);
     if (e == cudaSuccess && K > 1) e = cudaStreamWaitEvent(s, h->chunk_ev[k], 0);
     if (e != cudaSuccess) return finish(cuda_fail(e, "usaphmp_eval input copies"));
-    launch_canon(h->d_hubs_in + (size_t)c0 * h->p, h->d_S_in + (size_t)c0 * h->n, nb, h->n, h->p, h->ns,
-                 h->ev.hubs + (size_t)c0 * h->p, h->ev.slot + (size_t)c0 * h->ns, h->d_status, h->d_bad, s, c0);
     PopBuf pc = full;
     pc.B = nb;
     pc.hubs += (size_t)c0 * h->p;
@@ -882,8 +884,13 @@ int usaphmp_eval(usaphmp_t h, int32_t B, const int32_t* hubs, const int32_t* S, 
     pc.t12 += c0;
     pc.chub += (size_t)c0 * cst;
     const Task tc = make_task(h, pc);
-    TaskSet ts{nullptr, &tc, 1};
-    launch_alloc(ts, false, use_tc(h), s);
+    const int32_t* hin = h->d_hubs_in + (size_t)c0 * h->p;
+    const int32_t* sin = h->d_S_in + (size_t)c0 * h->n;
+    if (!launch_canon_alloc(tc, hin, sin, h->d_bad, c0, use_tc(h), s)) {
+      launch_canon(hin, sin, nb, h->n, h->p, h->ns, pc.hubs, pc.slot, h->d_status, h->d_bad, s, c0);
+      TaskSet ts{nullptr, &tc, 1};
+      launch_alloc(ts, false, use_tc(h), s);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return finish(cuda_fail(e, "usaphmp_eval allocation"));
   }
   if ((rc = run_transfer(h, make_task(h, full), s)) != USAPHMP_OK) return finish(rc);

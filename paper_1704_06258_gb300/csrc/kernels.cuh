@@ -121,6 +121,11 @@ void launch_canon(const int32_t* hubs_in, const int32_t* S, int B, int n, int p,
 // alloc.cu: nearest allocation (or the given slots), access terms t12 and
 // (with_chub) the hub-to-hub cost table chub.
 void launch_alloc(const TaskSet& ts, bool nearest, bool with_chub, cudaStream_t s);
+// Canonical form of chromosomes given as hub ids + S (validation, sorted hubs,
+// slot codes) fused with the given-slot allocation terms and hub-cost tables;
+// direct hub arcs only (returns false for hub-path routing, launching nothing).
+bool launch_canon_alloc(const Task& task, const int32_t* hubs_in, const int32_t* S, int* bad_index, int index_base,
+                        bool with_chub, cudaStream_t s);
 
 // eval_plain.cu: fp32 CUDA-core transfer sums into pop.part[r][b]; the
 // number of partial rows per task is plain_rows(n, B).
