@@ -43,8 +43,8 @@ PROFILED = {
                   "sha256": "a0116f664be45734f0a786db52d2e1cbf5139f4cd9bb59c1ca781c63870fce3f",
                   "dram_bytes": 13726000, "tensor_pipe_active": 0.616},
     "k_alloc": {"files": ["alloc.cu", "common.cuh"],
-                "sha256": "8985f1e9de9f08f60aad864c8a5c966e15d66e425da51b4e4d155a02469b5e8f",
-                "dram_bytes": 4359000, "alu_pipe_active": 0.578},
+                "sha256": "b3ec3bf00c541c262f33892c183982548591d4aa7ed3793a581494efcee328e9",
+                "dram_bytes": 4371000, "alu_pipe_active": 0.597},
 }
 # ALU lanes per SM (4 sub-partitions x 16 lanes of the integer / compare /
 # select pipe): the peak of the nearest-hub search, which is compares and
@@ -286,8 +286,25 @@ def e2e_eval(gi, inst, steps, warmup):
         f = gi.eval(hp, Sp)
     dt = time.perf_counter() - t0
     assert np.isfinite(f).all()
+    # the host link's share: the same bytes copied alone by the copy engine
+    # (pinned host -> device, CUDA events on a side stream)
+    st = torch.cuda.Stream()
+    dS = torch.empty(S.shape, dtype=torch.int32, device="cuda")
+    Sp_t = torch.from_numpy(Sp)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    copy_ms = []
+    for _ in range(5):
+        with torch.cuda.stream(st):
+            a.record(st)
+            dS.copy_(Sp_t, non_blocking=True)
+            b.record(st)
+        torch.cuda.synchronize()
+        copy_ms.append(a.elapsed_time(b))
+    copy_ms = float(np.median(copy_ms))
     return {"value": B * steps / dt, "unit": UNIT, "h2d_bytes_per_step": int(hubs.nbytes + S.nbytes),
-            "d2h_bytes_per_step": int(B * 8), "call": "usaphmp_eval (host hubs + S -> host fitness)"}
+            "d2h_bytes_per_step": int(B * 8), "call": "usaphmp_eval (host hubs + S -> host fitness)",
+            "ms_per_call": dt / steps * 1e3,
+            "s_copy_alone_ms": copy_ms, "s_copy_alone_gbs": S.nbytes / (copy_ms * 1e-3) / 1e9}
 
 
 def _make_request(r):
@@ -553,6 +570,17 @@ def run_ours(args):
     B = ISLANDS * ISLAND
     out = {}
     only_split = args.legs == "split"
+    if args.legs == "e2e":               # the host-buffer evaluation alone (profiling runs)
+        with Instance.from_instance(inst) as gi:
+            gi.set_params(islands=ISLANDS, island_size=ISLAND, n1=10, path=PATH_SPLIT_BF16)
+            if args.tile:
+                gi.set_tile(*(int(v) for v in args.tile.split(",")))
+            else:
+                gi.autotune(reps=20)
+            e2e = e2e_eval(gi, inst, steps=args.steps, warmup=args.warmup)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "legs": "e2e", "e2e": e2e}))
+        return
     with Instance.from_instance(inst) as gi:
         if not only_split:
             gi.set_params(islands=ISLANDS, island_size=ISLAND, n1=10, path=PATH_PLAIN_FP32)
@@ -710,8 +738,9 @@ def main():
     ap.add_argument("--tile", default="", help="fixed TC tile shape ntile,stages,raster[,pair] instead of the autotuner")
     ap.add_argument("--serve", type=int, default=512, help="serving requests (0 = skip the serving leg)")
     ap.add_argument("--large", type=int, default=1, help="also time the n=6000 configuration (0 = skip)")
-    ap.add_argument("--legs", choices=["all", "split"], default="all",
-                    help="split: only the timed split-bf16 generations (for profiling runs)")
+    ap.add_argument("--legs", choices=["all", "split", "e2e"], default="all",
+                    help="split: only the timed split-bf16 generations; e2e: only the host-buffer "
+                         "evaluation (both for profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

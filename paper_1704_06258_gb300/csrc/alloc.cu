@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(32 * kAllocWarps) k_alloc_warp(const __grid_co
       const float4* __restrict__ CT4 = reinterpret_cast<const float4*>(CT);
       int kp = 0;   // first hub not below the current group's first node
       for (int g = u0; g < n4; g += kAllocGroups * stride) {
-        float4 best[kAllocGroups];
+        float4 best[kAllocGroups], o4[kAllocGroups], d4[kAllocGroups];
         int sl[kAllocGroups][4];
         const float4* col[kAllocGroups];   // column group gj of CT (a valid one for a missing group)
 #pragma unroll
@@ -356,6 +356,8 @@ __global__ void __launch_bounds__(32 * kAllocWarps) k_alloc_warp(const __grid_co
           const int gj = g + j * stride;
           col[j] = CT4 + (gj < n4 ? gj : g);
           best[j] = __ldg(col[j] + ho[kHoPad]);
+          o4[j] = __ldg(reinterpret_cast<const float4*>(O) + (gj < n4 ? gj : g));
+          d4[j] = __ldg(reinterpret_cast<const float4*>(D) + (gj < n4 ? gj : g));
           sl[j][0] = sl[j][1] = sl[j][2] = sl[j][3] = 0;
         }
         int l = 1;
@@ -405,8 +407,6 @@ __global__ void __launch_bounds__(32 * kAllocWarps) k_alloc_warp(const __grid_co
               default: sl[j][3] = q; best[j].w = own; break;
             }
           }
-          const float4 o4 = __ldg(reinterpret_cast<const float4*>(O) + gj);
-          const float4 d4 = __ldg(reinterpret_cast<const float4*>(D) + gj);
           // one node of the group: access terms (in node order) and slot code
           auto node = [&](int k, int sk, float cih, float oi, float di) -> uint32_t {
             const int i = i0 + k;
@@ -415,10 +415,10 @@ __global__ void __launch_bounds__(32 * kAllocWarps) k_alloc_warp(const __grid_co
             acc += access_term(chi, oi, cih, delta, di, chi_i);
             return (uint32_t)sk << (8 * k);
           };
-          uint32_t packed = node(0, sl[j][0], best[j].x, o4.x, d4.x);
-          packed |= node(1, sl[j][1], best[j].y, o4.y, d4.y);
-          packed |= node(2, sl[j][2], best[j].z, o4.z, d4.z);
-          packed |= node(3, sl[j][3], best[j].w, o4.w, d4.w);
+          uint32_t packed = node(0, sl[j][0], best[j].x, o4[j].x, d4[j].x);
+          packed |= node(1, sl[j][1], best[j].y, o4[j].y, d4[j].y);
+          packed |= node(2, sl[j][2], best[j].z, o4[j].z, d4[j].z);
+          packed |= node(3, sl[j][3], best[j].w, o4[j].w, d4[j].w);
           *reinterpret_cast<uint32_t*>(slot + i0) = packed;
         }
       }
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(32 * kAllocWarps) k_alloc_warp(const __grid_co
   }
   if (live && wl == 0 && lane == 0) T.pop.t12[b] = acc;
   if (live && (with_chub || plain_global_table(p, ns)))
-    fill_chub<4>(T.pop.chub + (long long)b * chub_cstride(p), C, hs, p, ldw, u0, stride);
+    fill_chub<16>(T.pop.chub + (long long)b * chub_cstride(p), C, hs, p, ldw, u0, stride);
 }
 
 // Chromosomes given in the encoding of §4.1 (p hub node ids in any order and
