@@ -4,7 +4,7 @@ import zlib
 import numpy as np
 import pytest
 
-from gpu_util import dev, host, need_gpu, stream, torch
+from gpu_util import dev, host, need_gpu, stream, torch, unpack_masks
 from oracle import cost
 from paper_1704_06258_gb300 import synth
 from paper_1704_06258_gb300.binding import PATH_PLAIN_FP32, PATH_SPLIT_BF16, Instance, UsaphmpError
@@ -236,3 +236,26 @@ def test_folded_operand_follows_symmetry():
             info = gi.info()
             assert (info["c_symmetric"], info["tc_folded"]) == (folded, folded)
             assert (info["n"], info["p"], info["ns"]) == (inst.n, inst.p, gi.ns)
+
+
+@pytest.mark.parametrize("path", PATHS, ids=["plain", "split"])
+@pytest.mark.parametrize("n,R,P", [(1000, 8, 64), (2500, 4, 32)])
+def test_host_eval_of_ga_children_gives_the_ga_fitness(n, R, P, path):
+    """The GA's allocation kernel (nearest hub search) and the host-buffer
+    evaluation (canonical form of hub ids + S) sum the access terms in the same
+    order, so a child of the GA evaluated again through usaphmp_eval, with the
+    oracle's nearest allocation as its S, gets the GA's fitness bit for bit
+    (one warp per chromosome at n = 1000, two at n = 2500)."""
+    inst = synth.clustered(seed=2100 + n, n=n, p=20)
+    rng = np.random.default_rng(n)
+    with Instance.from_instance(inst) as gi:
+        gi.set_params(islands=R, island_size=P, n1=5, path=path)
+        gi.ga_begin(77)
+        gi.ga_run(3)
+        masks, fit = gi.ga_population()
+        bits = unpack_masks(masks, n)
+        idx = np.sort(rng.choice(R * P, 24, replace=False))
+        hubs = np.stack([np.flatnonzero(bits[b]) for b in idx]).astype(np.int32)
+        S = np.stack([cost.nearest_allocation(inst.C, h) for h in hubs]).astype(np.int32)
+        got = gi.eval(hubs[::-1].copy(), S[::-1].copy())[::-1]   # another order and batch
+    np.testing.assert_array_equal(got, fit[idx].astype(np.float64))
