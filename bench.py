@@ -40,10 +40,10 @@ CSRC = os.path.join(ROOT, "paper_1704_06258_gb300", "csrc")
 # to it (null otherwise: the kernel changed since the capture).
 PROFILED = {
     "k_eval_tc": {"files": ["eval_tc.cu", "tc_ptx.cuh", "common.cuh"],
-                  "sha256": "a0116f664be45734f0a786db52d2e1cbf5139f4cd9bb59c1ca781c63870fce3f",
+                  "sha256": "21c162630744f4554ec09b2f6f1a2587bbee5a729f7e7732e712952663a60017",
                   "dram_bytes": 13726000, "tensor_pipe_active": 0.616},
     "k_alloc": {"files": ["alloc.cu", "common.cuh"],
-                "sha256": "b3ec3bf00c541c262f33892c183982548591d4aa7ed3793a581494efcee328e9",
+                "sha256": "146052e0952bbe5b03365c18528d0f488fc238d99a12b6169efac19bf2477b1d",
                 "dram_bytes": 4371000, "alu_pipe_active": 0.597},
 }
 # ALU lanes per SM (4 sub-partitions x 16 lanes of the integer / compare /

@@ -12,10 +12,9 @@
 //                                  ns = n rounded up to 64, padding = 0xFF
 //   chub          fp32  [B][cstride]  hub-to-hub costs of chromosome b:
 //                 chub[b][k * hstride + l] = C[hubs_b[k], hubs_b[l]], rows of
-//                 hstride = 4 * (odd number) >= p floats: 16-byte aligned rows
-//                 whose 16-byte groups fall in distinct bank groups for
-//                 distinct k mod 8; cstride = p * hstride (aligned blocks for
-//                 bulk copies)
+//                 hstride = p | 1 floats (odd, so that 32 different rows fall
+//                 on 32 different shared-memory banks); cstride = p * hstride
+//                 rounded up to 4 (16-byte aligned tables for bulk copies)
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
