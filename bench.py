@@ -302,7 +302,8 @@ def e2e_eval(gi, inst, steps, warmup):
         copy_ms.append(a.elapsed_time(b))
     copy_ms = float(np.median(copy_ms))
     return {"value": B * steps / dt, "unit": UNIT, "h2d_bytes_per_step": int(hubs.nbytes + S.nbytes),
-            "d2h_bytes_per_step": int(B * 8), "call": "usaphmp_eval (host hubs + S -> host fitness)",
+            # fp32 fitness written by the device into pinned host memory + the 8-byte status read
+            "d2h_bytes_per_step": int(B * 4 + 8), "call": "usaphmp_eval (host hubs + S -> host fitness)",
             "ms_per_call": dt / steps * 1e3,
             "s_copy_alone_ms": copy_ms, "s_copy_alone_gbs": S.nbytes / (copy_ms * 1e-3) / 1e9}
 

@@ -145,8 +145,7 @@ struct usaphmp_s {
   Pop ev;
   int32_t* d_hubs_in = nullptr;
   int32_t* d_S_in = nullptr;
-  float* d_fit_out = nullptr;
-  float* h_fit_out = nullptr;        // pinned staging of the fitness returned by usaphmp_eval
+  float* h_fit_out = nullptr;        // pinned fitness of usaphmp_eval (written by the device through its mapping)
   int in_cap = 0;
 
   // GA
@@ -652,7 +651,7 @@ void usaphmp_destroy(usaphmp_t h) {
     if (h->h_bad) cudaFreeHost(h->h_bad);
   }
   h->ev.release(h->ac); h->ga.release(h->ac); h->one.release(h->ac);
-  dfree(h->ac, h->d_hubs_in); dfree(h->ac, h->d_S_in); dfree(h->ac, h->d_fit_out);
+  dfree(h->ac, h->d_hubs_in); dfree(h->ac, h->d_S_in);
   if (h->h_fit_out) cudaFreeHost(h->h_fit_out);
   dfree(h->ac, h->anc); dfree(h->ac, h->anc_fit); dfree(h->ac, h->best); dfree(h->ac, h->best_fit); dfree(h->ac, h->gen); dfree(h->ac, h->mask0);
   dfree(h->ac, h->done);
@@ -830,13 +829,12 @@ int usaphmp_eval(usaphmp_t h, int32_t B, const int32_t* hubs, const int32_t* S, 
   if (!hubs || !S || !fitness) return fail(USAPHMP_EINVAL, "NULL argument");
   cudaStream_t s = h->stream;
   if (h->in_cap < B) {
-    dfree(h->ac, h->d_hubs_in); dfree(h->ac, h->d_S_in); dfree(h->ac, h->d_fit_out);
+    dfree(h->ac, h->d_hubs_in); dfree(h->ac, h->d_S_in);
     if (h->h_fit_out) cudaFreeHost(h->h_fit_out);
     h->h_fit_out = nullptr;
     h->in_cap = 0;
     CK(dalloc(h->ac, &h->d_hubs_in, (size_t)B * h->p));
     CK(dalloc(h->ac, &h->d_S_in, (size_t)B * h->n));
-    CK(dalloc(h->ac, &h->d_fit_out, (size_t)B));
     CK(cudaMallocHost(&h->h_fit_out, sizeof(float) * B));
     h->in_cap = B;
   }
@@ -862,21 +860,34 @@ int usaphmp_eval(usaphmp_t h, int32_t B, const int32_t* hubs, const int32_t* S, 
   int rc = ensure_pop(h, h->ev, B);
   if (rc != USAPHMP_OK) return rc;
   if (use_fp64(h) && (rc = ensure_fp64(h, B)) != USAPHMP_OK) return rc;
+  // all copies first, back to back on the copy stream (hub ids whole, then S
+  // chunk by chunk, an event after each chunk), so the copy engine never
+  // waits for the host to enqueue the kernels
+  auto chunk = [&](int k, int& c0, int& nb) {
+    c0 = (int)((long long)B * k / K);
+    nb = (int)((long long)B * (k + 1) / K) - c0;
+  };
+  cudaError_t e = cudaMemcpyAsync(h->d_hubs_in, hubs, sizeof(int32_t) * (size_t)B * h->p, cudaMemcpyHostToDevice, cs);
+  for (int k = 0; k < K && e == cudaSuccess; ++k) {
+    int c0, nb;
+    chunk(k, c0, nb);
+    e = cudaMemcpyAsync(h->d_S_in + (size_t)c0 * h->n, S + (size_t)c0 * h->n, sizeof(int32_t) * nb * h->n,
+                        cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess && K > 1) e = cudaEventRecord(h->chunk_ev[k], cs);
+  }
+  if (e != cudaSuccess) return finish(cuda_fail(e, "usaphmp_eval input copies"));
   if ((rc = reset_status(h, s)) != USAPHMP_OK) return finish(rc);
   PopBuf full = popbuf(h, h->ev, B);
-  full.fit = h->d_fit_out;
+  // the reduction writes the fitness straight into the pinned host buffer
+  // (mapped into the device's address space): no copy-out
+  full.fit = h->h_fit_out;
   full.out_scale = (float)output_scale(h);
   const int cst = chub_cstride(h->p);
   for (int k = 0; k < K; ++k) {
-    const int c0 = (int)((long long)B * k / K), c1 = (int)((long long)B * (k + 1) / K), nb = c1 - c0;
-    cudaError_t e = cudaMemcpyAsync(h->d_hubs_in + (size_t)c0 * h->p, hubs + (size_t)c0 * h->p,
-                                    sizeof(int32_t) * nb * h->p, cudaMemcpyHostToDevice, cs);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(h->d_S_in + (size_t)c0 * h->n, S + (size_t)c0 * h->n, sizeof(int32_t) * nb * h->n,
-                          cudaMemcpyHostToDevice, cs);
-    if (e == cudaSuccess && K > 1) e = cudaEventRecord(h->chunk_ev[k], cs);
-    if (e == cudaSuccess && K > 1) e = cudaStreamWaitEvent(s, h->chunk_ev[k], 0);
-    if (e != cudaSuccess) return finish(cuda_fail(e, "usaphmp_eval input copies"));
+    int c0, nb;
+    chunk(k, c0, nb);
+    if (K > 1 && (e = cudaStreamWaitEvent(s, h->chunk_ev[k], 0)) != cudaSuccess)
+      return finish(cuda_fail(e, "usaphmp_eval input copies"));
     PopBuf pc = full;
     pc.B = nb;
     pc.hubs += (size_t)c0 * h->p;
@@ -894,8 +905,6 @@ int usaphmp_eval(usaphmp_t h, int32_t B, const int32_t* hubs, const int32_t* S, 
     if ((e = cudaGetLastError()) != cudaSuccess) return finish(cuda_fail(e, "usaphmp_eval allocation"));
   }
   if ((rc = run_transfer(h, make_task(h, full), s)) != USAPHMP_OK) return finish(rc);
-  cudaError_t e = cudaMemcpyAsync(h->h_fit_out, h->d_fit_out, sizeof(float) * B, cudaMemcpyDeviceToHost, s);
-  if (e != cudaSuccess) return finish(cuda_fail(e, "usaphmp_eval fitness copy"));
   if ((rc = check_status(h, s, "usaphmp_eval")) != USAPHMP_OK) return rc;   // one synchronisation
   for (int b = 0; b < B; ++b) fitness[b] = h->h_fit_out[b];
   return USAPHMP_OK;
