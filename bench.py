@@ -675,7 +675,7 @@ def run_ours(args):
                            "alu_pipe_active_ncu": profiled("k_alloc", "alu_pipe_active"),
                            "gathers": {"bytes_per_launch": a_bytes, "achieved_gbs": a_bytes / (a_ms * 1e-3) / 1e9,
                                        "l2_read_gbs_measured": l2_gbs,
-                                       "note": "C (4 MB) stays in L2 at n=1000 and 71 % of the hub-row reads hit L1: "
+                                       "note": "C (4 MB) stays in L2 at n=1000 and 70 % of the hub-row reads hit L1: "
                                                "the gathers are cache reads, not HBM traffic"}},
         "cpu_baseline": cpu1,
         "cpu_baseline_all_cores": cpu_baseline_all_cores(cpu1["per_step_s"]) if cpu1 else None,
