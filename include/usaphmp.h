@@ -149,10 +149,14 @@ typedef struct {
 } usaphmp_info;
 int usaphmp_get_info(usaphmp_t h, usaphmp_info* info);
 
-/* Fitness (objective 1, raw, unscaled) of B chromosomes given on the host:
- * hubs [B][p] node ids (any order), S [B][n] node ids; fitness [B] out.
- * Computed on the GPU by the configured path (fp32 arithmetic).  Returns
- * USAPHMP_EINVAL_CHROM naming the first invalid chromosome. */
+/* Fitness (objective 1 times the handle's output scale, raw by default) of B
+ * chromosomes given on the host in the encoding of §4.1: hubs [B][p] node ids
+ * (any order), S [B][n] node ids; fitness [B] out.  Computed on the GPU by the
+ * configured path (fp32 arithmetic): the inputs are copied in chunks, each
+ * chunk checked and put in canonical form as it lands, and the call returns
+ * once the fitness is on the host (the caller's buffers are not retained).
+ * Returns USAPHMP_EINVAL_CHROM naming the first invalid chromosome (eq. 2, 3,
+ * 5: distinct hubs, S[i] an open hub, every hub serving itself). */
 int usaphmp_eval(usaphmp_t h, int32_t B, const int32_t* hubs, const int32_t* S, double* fitness);
 
 /* Same with device arrays; fitness is fp32 [B].  Validation needs the device
