@@ -264,3 +264,56 @@ def test_solve_graph_and_eager_agree(use_graph):
     np.testing.assert_array_equal(out[0]["hubs"], out[1]["hubs"])
     assert out[0]["cost_fp32"] == out[1]["cost_fp32"]
     assert out[0]["cost_fp64"] == out[1]["cost_fp64"]
+
+
+def _asym(seed, n, p):
+    rng = np.random.default_rng(seed)
+    W = rng.uniform(0, 5, (n, n)).astype(np.float32)
+    C = rng.uniform(1, 50, (n, n)).astype(np.float32)
+    np.fill_diagonal(C, 0)
+    return synth.Instance(f"asym{n}", n, p, W, C)
+
+
+@pytest.mark.parametrize("n,p,B", [(150, 6, 40), (333, 7, 24)])
+def test_allocation_bit_exact_asymmetric_c(n, p, B):
+    """Nearest allocation compares C[i][hub] (row i), which differs from
+    C[hub][i] here: the kernel's transposed reads must pick the oracle's hubs."""
+    inst = _asym(n + 3, n, p)
+    masks = synth.random_masks(n + 4, n, p, B)
+    hubs = np.stack([np.flatnonzero(m) for m in masks]).astype(np.int32)
+    with Instance.from_instance(inst) as gi:
+        slot = torch.zeros((B, gi.ns), dtype=torch.uint8, device="cuda")
+        d_hubs = dev(hubs)
+        gi.allocate_dev(B, d_hubs.data_ptr(), slot.data_ptr(), stream())
+        got = host(slot)
+    for b in range(B):
+        ref = cost.slots_of(hubs[b], cost.nearest_allocation(inst.C, hubs[b]))
+        np.testing.assert_array_equal(got[b, :n], ref)
+
+
+@pytest.mark.parametrize("path", [PATH_PLAIN_FP32, PATH_SPLIT_BF16], ids=["plain", "split"])
+def test_ga_run_on_asymmetric_c_follows_the_oracle(path):
+    """The graph-replayed generation on an asymmetric C (the tensor cores take
+    the unfolded W): every generation's children equal the oracle's, their
+    fitness is within the path's tolerance of the fp64 objective, and the
+    ancestors after selection are the oracle's, fed the GPU's fitness."""
+    n, p, R, P, N1, seed, G = 150, 6, 4, 8, 2, 515, 3
+    inst = _asym(41, n, p)
+    with Instance.from_instance(inst) as gi:
+        gi.set_params(islands=R, island_size=P, n1=N1, path=path, use_graph=1)
+        assert gi.info()["tc_folded"] == 0
+        gi.ga_begin(seed)
+        am, af = gi.ga_islands()
+        st = ga.State(unpack_masks(am, n), af.astype(np.float64), unpack_masks(am, n)[0], float(af[0]))
+        for g in range(G):
+            gi.ga_run(1)
+            masks, fit = gi.ga_population()
+            children = ga.make_children(st.ancestors, seed, g, p, P)
+            np.testing.assert_array_equal(unpack_masks(masks, n), children)
+            _, hh, _ = ga.allocate_all(inst.C, children)
+            ref = np.array([cost.pair_cost(inst.W, inst.C, inst.chi, inst.alpha, inst.delta, x) for x in hh])
+            assert (np.abs(fit - ref) / ref).max() <= (1e-5 if path == PATH_PLAIN_FP32 else 1e-4)
+            ga.select(st, children, fit.astype(np.float64), g, P, N1)
+            am, af = gi.ga_islands()
+            np.testing.assert_array_equal(unpack_masks(am, n), st.ancestors)
+            np.testing.assert_array_equal(af, st.anc_fit.astype(np.float32))
