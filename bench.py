@@ -40,11 +40,11 @@ CSRC = os.path.join(ROOT, "paper_1704_06258_gb300", "csrc")
 # to it (null otherwise: the kernel changed since the capture).
 PROFILED = {
     "k_eval_tc": {"files": ["eval_tc.cu", "tc_ptx.cuh", "common.cuh"],
-                  "sha256": "21c162630744f4554ec09b2f6f1a2587bbee5a729f7e7732e712952663a60017",
-                  "dram_bytes": 13726000, "tensor_pipe_active": 0.616},
+                  "sha256": "5d6817ec87e1505f3ceed147eca04a342b0e3bafb2d15720a67ca9c10a88c600",
+                  "dram_bytes": 13727000, "tensor_pipe_active": 0.618},
     "k_alloc": {"files": ["alloc.cu", "common.cuh"],
-                "sha256": "146052e0952bbe5b03365c18528d0f488fc238d99a12b6169efac19bf2477b1d",
-                "dram_bytes": 4371000, "alu_pipe_active": 0.597},
+                "sha256": "c2aa14ed3dbe79d41eef5c64f5d8181404bfe24b6fe7b07221c53a27521b0bcf",
+                "dram_bytes": 4371000, "alu_pipe_active": 0.598},
 }
 # ALU lanes per SM (4 sub-partitions x 16 lanes of the integer / compare /
 # select pipe): the peak of the nearest-hub search, which is compares and

@@ -268,6 +268,8 @@ PopBuf popbuf(const usaphmp_s* h, const Pop& P, int B) {
   pb.slot_in = nullptr;
   pb.status = h->d_status;
   pb.out_scale = 1.0f;
+  pb.status_host = nullptr;
+  pb.bad = h->d_bad;
   return pb;
 }
 
@@ -289,17 +291,22 @@ Task make_task(const usaphmp_s* h, const PopBuf& pb) {
   return t;
 }
 
+// The error a device status word (and the index of the first invalid
+// chromosome) stands for.
+int status_error(uint32_t st, int bad, const char* what) {
+  if (st & kStatusTimeout) return fail(USAPHMP_ETIMEOUT, std::string(what) + ": a device wait timed out");
+  if (st & kStatusBadChromosome)
+    return fail(USAPHMP_EINVAL_CHROM, std::string(what) + ": chromosome " + std::to_string(bad) +
+                                          " is not a valid single allocation (distinct hubs, S[i] an open hub, S[hub] = hub)");
+  if (st & kStatusBadValue) return fail(USAPHMP_EINVAL, std::string(what) + ": W or C has a negative or non-finite entry");
+  return USAPHMP_OK;
+}
+
 int check_status(usaphmp_s* h, cudaStream_t s, const char* what) {
   CK(cudaMemcpyAsync(h->h_status, h->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(h->h_bad, h->d_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  const uint32_t st = *h->h_status;
-  if (st & kStatusTimeout) return fail(USAPHMP_ETIMEOUT, std::string(what) + ": a device wait timed out");
-  if (st & kStatusBadChromosome)
-    return fail(USAPHMP_EINVAL_CHROM, std::string(what) + ": chromosome " + std::to_string(*h->h_bad) +
-                                          " is not a valid single allocation (distinct hubs, S[i] an open hub, S[hub] = hub)");
-  if (st & kStatusBadValue) return fail(USAPHMP_EINVAL, std::string(what) + ": W or C has a negative or non-finite entry");
-  return USAPHMP_OK;
+  return status_error(*h->h_status, *h->h_bad, what);
 }
 
 int reset_status(usaphmp_s* h, cudaStream_t s) {
@@ -835,7 +842,7 @@ int usaphmp_eval(usaphmp_t h, int32_t B, const int32_t* hubs, const int32_t* S, 
     h->in_cap = 0;
     CK(dalloc(h->ac, &h->d_hubs_in, (size_t)B * h->p));
     CK(dalloc(h->ac, &h->d_S_in, (size_t)B * h->n));
-    CK(cudaMallocHost(&h->h_fit_out, sizeof(float) * B));
+    CK(cudaMallocHost(&h->h_fit_out, sizeof(float) * ((size_t)B + 2)));   // + the two status words
     h->in_cap = B;
   }
   // The inputs arrive in K chunks on a copy stream; the canonical form and
@@ -878,9 +885,12 @@ int usaphmp_eval(usaphmp_t h, int32_t B, const int32_t* hubs, const int32_t* S, 
   if (e != cudaSuccess) return finish(cuda_fail(e, "usaphmp_eval input copies"));
   if ((rc = reset_status(h, s)) != USAPHMP_OK) return finish(rc);
   PopBuf full = popbuf(h, h->ev, B);
-  // the reduction writes the fitness straight into the pinned host buffer
-  // (mapped into the device's address space): no copy-out
+  // the reduction writes the fitness, then the status words, straight into
+  // the pinned host buffer (mapped into the device's address space): no
+  // copy-out (the fp64 reference path reads the status with copies)
   full.fit = h->h_fit_out;
+  uint32_t* st_host = reinterpret_cast<uint32_t*>(h->h_fit_out + B);
+  if (!use_fp64(h)) full.status_host = st_host;
   full.out_scale = (float)output_scale(h);
   const int cst = chub_cstride(h->p);
   for (int k = 0; k < K; ++k) {
@@ -905,7 +915,12 @@ int usaphmp_eval(usaphmp_t h, int32_t B, const int32_t* hubs, const int32_t* S, 
     if ((e = cudaGetLastError()) != cudaSuccess) return finish(cuda_fail(e, "usaphmp_eval allocation"));
   }
   if ((rc = run_transfer(h, make_task(h, full), s)) != USAPHMP_OK) return finish(rc);
-  if ((rc = check_status(h, s, "usaphmp_eval")) != USAPHMP_OK) return rc;   // one synchronisation
+  if (full.status_host) {   // one synchronisation, then the words the reduction wrote
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return finish(cuda_fail(e, "usaphmp_eval"));
+    if ((rc = status_error(st_host[0], (int)st_host[1], "usaphmp_eval")) != USAPHMP_OK) return rc;
+  } else if ((rc = check_status(h, s, "usaphmp_eval")) != USAPHMP_OK) {
+    return rc;
+  }
   for (int b = 0; b < B; ++b) fitness[b] = h->h_fit_out[b];
   return USAPHMP_OK;
 }

@@ -94,6 +94,11 @@ struct PopBuf {
   float* fit;      // fp32 fitness
   uint32_t* status;  // device status word (kStatus* bits)
   float out_scale;   // factor k_reduce applies to the fitness it writes (1: raw cost)
+  // Optional pinned host words k_reduce fills after the evaluation: [0] the
+  // status word, [1] the index of the first invalid chromosome (`bad`), so a
+  // host call reads them without copies of its own.
+  uint32_t* status_host;
+  const int* bad;
 };
 
 // Island GA state (§5): R islands of P chromosomes.

@@ -15,6 +15,11 @@ __global__ void k_reduce(const __grid_constant__ TaskParam tp) {
   const Task& T = task_at(tp, t);
   const int b = (blockIdx.x - tp.bo.o[t]) * blockDim.x + threadIdx.x;
   const int B = T.pop.B;
+  // every kernel that can raise the status ran before this one
+  if (b == 0 && T.pop.status_host) {
+    T.pop.status_host[0] = *T.pop.status;
+    T.pop.status_host[1] = (uint32_t)*T.pop.bad;
+  }
   if (b >= B) return;
   const float s = sum_rows_in_order(T.pop.part + b, T.pop.npart, B);
   T.pop.fit[b] = (T.pop.t12[b] + T.in.alpha * s) * T.pop.out_scale;
