@@ -42,16 +42,42 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
   return c;
 }
 
+// The Philox blocks a warp's operators draw from, computed at once, one per
+// lane (lane 0: exchange block 0; 1: the pair's crossover block 0; 2:
+// mutation block 0; 3..31: correction blocks 0..28).  A stream's later
+// blocks, beyond the table, are computed when needed.
+constexpr int kTableCorrection = 29;
+__device__ __forceinline__ int table_lane(uint32_t op, uint32_t d) {
+  if (op == kOpExchange) return d == 0 ? 0 : -1;
+  if (op == kOpCrossover) return d == 0 ? 1 : -1;
+  if (op == kOpMutation) return d == 0 ? 2 : -1;
+  return d < (uint32_t)kTableCorrection ? 3 + (int)d : -1;
+}
+
+__device__ __forceinline__ uint32_t word_of(const uint4& b, int i) {
+  return i == 0 ? b.x : i == 1 ? b.y : i == 2 ? b.z : b.w;
+}
+
+// One operator's stream of 32-bit draws (warp-uniform calls): words of block
+// d = 0, 1, ... in order, taken from the warp's table while it holds them.
 struct Draws {
   uint4 ctr;
   uint2 key;
   uint4 buf;
   int used;
-  __device__ Draws(unsigned long long seed, uint32_t g, uint32_t q, uint32_t op)
-      : ctr(make_uint4(g, q, op, 0u)), key(make_uint2((uint32_t)seed, (uint32_t)(seed >> 32))), used(4) {}
+  int src;               // lane holding the current block, -1: computed into buf
+  const uint4* table;    // this lane's table block
+  __device__ Draws(unsigned long long seed, uint32_t g, uint32_t q, uint32_t op, const uint4* mine)
+      : ctr(make_uint4(g, q, op, 0u)), key(make_uint2((uint32_t)seed, (uint32_t)(seed >> 32))), used(4), src(-1),
+        table(mine) {}
   __device__ uint32_t word() {
-    if (used == 4) { buf = philox4x32_10(ctr, key); ctr.w += 1u; used = 0; }
-    const uint32_t w = used == 0 ? buf.x : used == 1 ? buf.y : used == 2 ? buf.z : buf.w;
+    if (used == 4) {
+      src = table_lane(ctr.z, ctr.w);
+      if (src < 0) buf = philox4x32_10(ctr, key);
+      ctr.w += 1u;
+      used = 0;
+    }
+    const uint32_t w = src >= 0 ? __shfl_sync(0xffffffffu, word_of(*table, used), src) : word_of(buf, used);
     ++used;
     return w;
   }
@@ -155,6 +181,14 @@ __global__ void __launch_bounds__(64) k_children(const __grid_constant__ TaskPar
   uint32_t* par = msm + w * nw;
   uint32_t* oth = msm + (1 - w) * nw;
   uint32_t* ch = msm + (2 + w) * nw;
+  // the warp's Philox table (see table_lane), all blocks computed side by side
+  uint4 mine;
+  {
+    const uint32_t op = lane == 0 ? kOpExchange : lane == 1 ? kOpCrossover : lane == 2 ? kOpMutation : kOpCorrection;
+    const uint32_t qq = goff + (uint32_t)(lane == 1 ? q0 : q);
+    const uint32_t d = lane < 3 ? 0u : (uint32_t)(lane - 3);
+    mine = philox4x32_10(make_uint4(g, qq, op, d), make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+  }
 
   for (int x = lane; x < nw; x += 32) {
     uint32_t v = T.ga.anc[(long long)r * nw + x];
@@ -163,12 +197,12 @@ __global__ void __launch_bounds__(64) k_children(const __grid_constant__ TaskPar
   }
   __syncwarp();
   {
-    Draws d(seed, g, goff + (uint32_t)q, kOpExchange);
+    Draws d(seed, g, goff + (uint32_t)q, kOpExchange, &mine);
     exchange(par, nw, n, d);
   }
   __syncthreads();
   {
-    Draws d(seed, g, goff + (uint32_t)q0, kOpCrossover);
+    Draws d(seed, g, goff + (uint32_t)q0, kOpCrossover, &mine);
     const int c = 1 + (int)d.below((uint32_t)(n - 1));
     for (int x = lane; x < nw; x += 32) {
       const uint32_t own = par[x], other = oth[x];
@@ -185,11 +219,11 @@ __global__ void __launch_bounds__(64) k_children(const __grid_constant__ TaskPar
     __syncwarp();
   }
   {
-    Draws d(seed, g, goff + (uint32_t)q, kOpMutation);
+    Draws d(seed, g, goff + (uint32_t)q, kOpMutation, &mine);
     exchange(ch, nw, n, d);
   }
   {
-    Draws d(seed, g, goff + (uint32_t)q, kOpCorrection);
+    Draws d(seed, g, goff + (uint32_t)q, kOpCorrection, &mine);
     correct(ch, nw, n, p, d);
   }
   uint32_t* out = T.pop.mask + (long long)q * nw;
