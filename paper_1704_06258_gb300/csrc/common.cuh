@@ -146,10 +146,17 @@ __device__ inline float warp_sum(float v) {
 }
 
 // sum_{r < rows} x[r * stride], added in ascending r (the fixed order every
-// evaluator's partial sums are reduced in), loads issued sixteen at a time.
+// evaluator's partial sums are reduced in), loads issued 32 at a time.
 __device__ __forceinline__ float sum_rows_in_order(const float* __restrict__ x, int rows, long long stride) {
   float s = 0.f;
   int r = 0;
+  for (; r + 32 <= rows; r += 32) {
+    float v[32];
+#pragma unroll
+    for (int u = 0; u < 32; ++u) v[u] = x[(long long)(r + u) * stride];
+#pragma unroll
+    for (int u = 0; u < 32; ++u) s += v[u];
+  }
   for (; r + 16 <= rows; r += 16) {
     float v[16];
 #pragma unroll
