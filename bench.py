@@ -571,6 +571,14 @@ def run_ours(args):
     B = ISLANDS * ISLAND
     out = {}
     only_split = args.legs == "split"
+    if args.legs == "plain":             # the plain fp32 generations alone (profiling runs)
+        with Instance.from_instance(inst) as gp:
+            gp.set_params(islands=ISLANDS, island_size=ISLAND, n1=10, path=PATH_PLAIN_FP32)
+            st, _, _ = timed_generations(gp, args.steps, args.warmup, flush, stream, world)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "legs": "plain", "workload": WORKLOAD,
+                              "stage_ms": {k: round(v, 5) for k, v in st.items()}}))
+        return
     if args.legs == "large":             # n=6000, p=20 split-bf16 generations alone (profiling runs)
         from paper_1704_06258_gb300.binding import Instance as Inst
         big = synth.large_uniform(p=20)
@@ -753,9 +761,10 @@ def main():
     ap.add_argument("--tile", default="", help="fixed TC tile shape ntile,stages,raster[,pair] instead of the autotuner")
     ap.add_argument("--serve", type=int, default=512, help="serving requests (0 = skip the serving leg)")
     ap.add_argument("--large", type=int, default=1, help="also time the n=6000 configuration (0 = skip)")
-    ap.add_argument("--legs", choices=["all", "split", "e2e", "large"], default="all",
+    ap.add_argument("--legs", choices=["all", "split", "e2e", "large", "plain"], default="all",
                     help="split: only the timed split-bf16 generations; e2e: only the host-buffer "
-                         "evaluation; large: only n=6000 split-bf16 generations (all three for profiling runs)")
+                         "evaluation; large: only n=6000 split-bf16 generations; plain: only the plain fp32 "
+                         "generations (all four for profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
