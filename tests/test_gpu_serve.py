@@ -183,3 +183,45 @@ def test_serving_workload_alone_equals_the_poisson_mix():
         cost.check_allocation(inst.n, m["hubs"], m["S"])
         ref = cost.pair_cost(inst.W, inst.C, inst.chi, inst.alpha, inst.delta, m["S"])
         assert m["cost_fp64"] == pytest.approx(ref, rel=1e-12)
+
+
+def _asym(seed, n, p):
+    rng = np.random.default_rng(seed)
+    W = rng.uniform(0, 5, (n, n)).astype(np.float32)
+    C = rng.uniform(1, 50, (n, n)).astype(np.float32)
+    np.fill_diagonal(C, 0)
+    return synth.Instance(f"asym{n}", n, p, W, C)
+
+
+def test_asymmetric_requests_alone_equal_the_mix_and_a_direct_solve():
+    """Requests with an asymmetric C (unfolded tensor-core operand, transposed
+    copy of C) served beside symmetric ones: each result equals the request
+    served alone and a direct solve on a handle, and its fp64 cost is the
+    oracle's objective of the returned allocation."""
+    reqs = [(_asym(7300, 120, 6), 8, 31), (synth.clustered(seed=7301, n=150, p=8), 7, 32),
+            (_asym(7302, 75, 4), 10, 33), (synth.clustered(seed=7303, n=90, p=5), 9, 34)]
+    alone = []
+    for inst, gens, seed in reqs:
+        with Server(4 * GB, max_active=4, path=PATH_SPLIT_BF16) as s:
+            t = s.submit(inst.W, inst.C, inst.p, islands=2, island_size=16, generations=gens, seed=seed)
+            alone.append(_drain(s, [t])[t])
+    with Server(4 * GB, max_active=4, path=PATH_SPLIT_BF16) as s:
+        tickets = []
+        for k, (inst, gens, seed) in enumerate(reqs):
+            tickets.append(s.submit(inst.W, inst.C, inst.p, islands=2, island_size=16, generations=gens, seed=seed))
+            if k % 2:
+                s.step()
+        mixed = _drain(s, list(tickets))
+    for (inst, gens, seed), a, t in zip(reqs, alone, tickets):
+        m = mixed[t]
+        np.testing.assert_array_equal(a["hubs"], m["hubs"])
+        np.testing.assert_array_equal(a["S"], m["S"])
+        assert a["cost_fp32"] == m["cost_fp32"] and a["cost_fp64"] == m["cost_fp64"]
+        ref = cost.pair_cost(inst.W, inst.C, inst.chi, inst.alpha, inst.delta, m["S"])
+        assert m["cost_fp64"] == pytest.approx(ref, rel=1e-12)
+    inst, gens, seed = reqs[0]
+    with Instance.from_instance(inst) as gi:
+        gi.set_params(islands=2, island_size=16, n1=10, path=PATH_SPLIT_BF16)
+        direct = gi.solve(gens, seed)
+    np.testing.assert_array_equal(direct["hubs"], mixed[tickets[0]]["hubs"])
+    assert direct["cost_fp32"] == mixed[tickets[0]]["cost_fp32"]
