@@ -317,3 +317,30 @@ def test_ga_run_on_asymmetric_c_follows_the_oracle(path):
             am, af = gi.ga_islands()
             np.testing.assert_array_equal(unpack_masks(am, n), st.ancestors)
             np.testing.assert_array_equal(af, st.anc_fit.astype(np.float32))
+
+
+@pytest.mark.parametrize("path", [PATH_PLAIN_FP32, PATH_SPLIT_BF16], ids=["plain", "split"])
+@pytest.mark.parametrize("n,p", [(260, 100), (300, 230)])
+def test_ga_run_with_large_p_follows_the_oracle(n, p, path):
+    """Large p: hub-cost tables too big for the shared slab (p = 100, the
+    tensor-core epilogue reads them from global memory) or for the plain
+    evaluator's shared table (p = 230); the graph-replayed generations still
+    follow the oracle generation by generation."""
+    R, P, N1, seed, G = 2, 8, 2, 909, 3
+    inst = synth.urand200(seed=n + p, n=n, p=p)
+    with Instance.from_instance(inst) as gi:
+        gi.set_params(islands=R, island_size=P, n1=N1, path=path, use_graph=1)
+        gi.ga_begin(seed)
+        am, af = gi.ga_islands()
+        st = ga.State(unpack_masks(am, n), af.astype(np.float64), unpack_masks(am, n)[0], float(af[0]))
+        for g in range(G):
+            gi.ga_run(1)
+            masks, fit = gi.ga_population()
+            children = ga.make_children(st.ancestors, seed, g, p, P)
+            np.testing.assert_array_equal(unpack_masks(masks, n), children)
+            _, hh, _ = ga.allocate_all(inst.C, children)
+            ref = np.array([cost.pair_cost(inst.W, inst.C, inst.chi, inst.alpha, inst.delta, x) for x in hh])
+            assert (np.abs(fit - ref) / ref).max() <= (1e-5 if path == PATH_PLAIN_FP32 else 1e-4)
+            ga.select(st, children, fit.astype(np.float64), g, P, N1)
+            am, af = gi.ga_islands()
+            np.testing.assert_array_equal(unpack_masks(am, n), st.ancestors)
