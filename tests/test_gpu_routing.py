@@ -5,8 +5,8 @@ import zlib
 import numpy as np
 import pytest
 
-from gpu_util import dev, host, need_gpu, stream, torch
-from oracle import brute, cost
+from gpu_util import dev, host, need_gpu, stream, torch, unpack_masks
+from oracle import brute, cost, ga
 from paper_1704_06258_gb300 import synth
 from paper_1704_06258_gb300.binding import (PATH_PLAIN_FP32, PATH_SPLIT_BF16, ROUTE_DIRECT, ROUTE_HUB_PATHS,
                                             Instance, UsaphmpError)
@@ -108,3 +108,29 @@ def test_unknown_routing_is_refused():
             gi.set_params(routing=2)
         assert e.value.name == "EINVAL"
         assert gi.params["routing"] == ROUTE_DIRECT
+
+
+@pytest.mark.parametrize("path", PATHS, ids=["plain", "split"])
+def test_ga_run_with_hub_paths_follows_the_oracle(path):
+    """Graph-replayed generations with hub-path routing (the block allocation
+    kernel relaxes every chromosome's hub table): children equal the oracle's,
+    fitness within the path's tolerance of the oracle's routed objective, and
+    the ancestors after selection equal the oracle's, generation by generation."""
+    n, p, R, P, N1, seed, G = 150, 12, 2, 16, 2, 4141, 3
+    inst = synth.latency_like(seed=74, n=n, p=p, spread=1.0)
+    with Instance.from_instance(inst) as gi:
+        gi.set_params(islands=R, island_size=P, n1=N1, path=path, routing=ROUTE_HUB_PATHS, use_graph=1)
+        gi.ga_begin(seed)
+        am, af = gi.ga_islands()
+        st = ga.State(unpack_masks(am, n), af.astype(np.float64), unpack_masks(am, n)[0], float(af[0]))
+        for g in range(G):
+            gi.ga_run(1)
+            masks, fit = gi.ga_population()
+            children = ga.make_children(st.ancestors, seed, g, p, P)
+            np.testing.assert_array_equal(unpack_masks(masks, n), children)
+            _, hh, _ = ga.allocate_all(inst.C, children)
+            ref = oracle_costs(inst, hh, "hubs")
+            assert (np.abs(fit - ref) / ref).max() <= TOL[path]
+            ga.select(st, children, fit.astype(np.float64), g, P, N1)
+            am, af = gi.ga_islands()
+            np.testing.assert_array_equal(unpack_masks(am, n), st.ancestors)
