@@ -344,3 +344,30 @@ def test_ga_run_with_large_p_follows_the_oracle(n, p, path):
             ga.select(st, children, fit.astype(np.float64), g, P, N1)
             am, af = gi.ga_islands()
             np.testing.assert_array_equal(unpack_masks(am, n), st.ancestors)
+
+
+@pytest.mark.parametrize("path", [PATH_PLAIN_FP32, PATH_SPLIT_BF16], ids=["plain", "split"])
+def test_ga_run_elitist_follows_the_oracle(path):
+    """The fused reduction + selection of the replayed generation with the
+    elitist flag (an ancestor is kept unless a child is strictly better) and
+    merges every second generation: ancestors and their fitness after every
+    generation, and the best-ever solution at the end, equal the oracle's."""
+    n, p, R, P, N1, seed, G = 120, 6, 3, 8, 2, 6161, 6
+    inst = synth.urand200(seed=19, n=n, p=p)
+    with Instance.from_instance(inst) as gi:
+        gi.set_params(islands=R, island_size=P, n1=N1, path=path, elitist=1, use_graph=1)
+        gi.ga_begin(seed)
+        am, af = gi.ga_islands()
+        st = ga.State(unpack_masks(am, n), af.astype(np.float64), unpack_masks(am, n)[0], float(af[0]))
+        for g in range(G):
+            gi.ga_run(1)
+            masks, fit = gi.ga_population()
+            children = ga.make_children(st.ancestors, seed, g, p, P)
+            np.testing.assert_array_equal(unpack_masks(masks, n), children)
+            ga.select(st, children, fit.astype(np.float64), g, P, N1, elitist=True)
+            am, af = gi.ga_islands()
+            np.testing.assert_array_equal(unpack_masks(am, n), st.ancestors)
+            np.testing.assert_array_equal(af, st.anc_fit.astype(np.float32))
+        res = gi.ga_result()
+    np.testing.assert_array_equal(res["hubs"], np.flatnonzero(st.best))
+    assert np.float32(res["cost_fp32"]) == np.float32(st.best_fit)
